@@ -1,0 +1,115 @@
+/*
+ * Oracle (test infrastructure only): Roe Riemann solver for the 2D shallow
+ * water equations, Sec. 3 Eq. SW, with the Harten-Hyman entropy fix.
+ *
+ * Reduced state along a direction: q = (h, h u_n, h u_t).  Flux along that
+ * direction: f(q) = (h u_n, h u_n^2 + g h^2 / 2, h u_n u_t).
+ *
+ * Roe averages:  h_bar = (h_l + h_r) / 2,
+ *                u_hat = (sqrt(h_l) u_l + sqrt(h_r) u_r) / (sqrt(h_l) + sqrt(h_r)),
+ *                v_hat likewise for the transverse velocity,
+ *                c_hat = sqrt(g h_bar).
+ * Speeds s = (u_hat - c_hat, u_hat, u_hat + c_hat); eigenvectors
+ * r1 = (1, u_hat - c_hat, v_hat), r2 = (0, 0, 1), r3 = (1, u_hat + c_hat, v_hat);
+ * strengths from dq = sum_p alpha_p r_p.
+ *
+ * Fluctuations: A-dQ = sum min(s_p,0) W_p, A+dQ = sum max(s_p,0) W_p, except
+ * for a transonic rarefaction in the 1- or 3-family, which Harten-Hyman splits:
+ *   1-wave: lam_l = u_l - sqrt(g h_l), middle state q_m = Q_l + W1,
+ *           lam_m = u_m - sqrt(g h_m); if lam_l < 0 < lam_m then with
+ *           beta = (lam_m - s1) / (lam_m - lam_l)
+ *           A-dQ gets beta lam_l W1 and A+dQ gets (1 - beta) lam_m W1.
+ *   3-wave: q_m = Q_r - W3, lam_m = u_m + sqrt(g h_m), lam_r = u_r + sqrt(g h_r);
+ *           if lam_m < 0 < lam_r then beta = (lam_r - s3) / (lam_r - lam_m),
+ *           A-dQ gets beta lam_m W3 and A+dQ gets (1 - beta) lam_r W3.
+ * The shear (2-) wave is never fixed.  Either way A-dQ + A+dQ = sum s_p W_p.
+ */
+#include <math.h>
+#include "orc.h"
+
+void orc_rp_shallow_water(const double *ql, const double *qr, double g,
+                          double W[3][3], double s[3], double amdq[3], double apdq[3])
+{
+    double h_l = ql[0], h_r = qr[0];
+    double u_l = ql[1] / h_l, u_r = qr[1] / h_r;
+    double v_l = ql[2] / h_l, v_r = qr[2] / h_r;
+    double sqh_l = sqrt(h_l), sqh_r = sqrt(h_r);
+
+    double h_bar = 0.5 * (h_l + h_r);
+    double u_hat = (sqh_l * u_l + sqh_r * u_r) / (sqh_l + sqh_r);
+    double v_hat = (sqh_l * v_l + sqh_r * v_r) / (sqh_l + sqh_r);
+    double c_hat = sqrt(g * h_bar);
+
+    double d0 = qr[0] - ql[0];
+    double d1 = qr[1] - ql[1];
+    double d2 = qr[2] - ql[2];
+
+    double alpha1 = ((u_hat + c_hat) * d0 - d1) / (2.0 * c_hat);
+    double alpha2 = d2 - v_hat * d0;
+    double alpha3 = (d1 - (u_hat - c_hat) * d0) / (2.0 * c_hat);
+
+    s[0] = u_hat - c_hat;
+    s[1] = u_hat;
+    s[2] = u_hat + c_hat;
+
+    W[0][0] = alpha1;
+    W[0][1] = alpha1 * (u_hat - c_hat);
+    W[0][2] = alpha1 * v_hat;
+
+    W[1][0] = 0.0;
+    W[1][1] = 0.0;
+    W[1][2] = alpha2;
+
+    W[2][0] = alpha3;
+    W[2][1] = alpha3 * (u_hat + c_hat);
+    W[2][2] = alpha3 * v_hat;
+
+    for (int c = 0; c < 3; ++c) {
+        amdq[c] = 0.0;
+        apdq[c] = 0.0;
+    }
+
+    /* 1-wave */
+    {
+        double lam_l = u_l - sqrt(g * h_l);
+        double h_m = h_l + W[0][0];
+        double hu_m = ql[1] + W[0][1];
+        double lam_m = hu_m / h_m - sqrt(g * h_m);
+        if (lam_l < 0.0 && 0.0 < lam_m) {
+            double beta = (lam_m - s[0]) / (lam_m - lam_l);
+            for (int c = 0; c < 3; ++c) {
+                amdq[c] += beta * lam_l * W[0][c];
+                apdq[c] += (1.0 - beta) * lam_m * W[0][c];
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                if (s[0] < 0.0) amdq[c] += s[0] * W[0][c];
+                else            apdq[c] += s[0] * W[0][c];
+            }
+        }
+    }
+    /* 2-wave (shear) */
+    for (int c = 0; c < 3; ++c) {
+        if (s[1] < 0.0) amdq[c] += s[1] * W[1][c];
+        else            apdq[c] += s[1] * W[1][c];
+    }
+    /* 3-wave */
+    {
+        double lam_r = u_r + sqrt(g * h_r);
+        double h_m = h_r - W[2][0];
+        double hu_m = qr[1] - W[2][1];
+        double lam_m = hu_m / h_m + sqrt(g * h_m);
+        if (lam_m < 0.0 && 0.0 < lam_r) {
+            double beta = (lam_r - s[2]) / (lam_r - lam_m);
+            for (int c = 0; c < 3; ++c) {
+                amdq[c] += beta * lam_m * W[2][c];
+                apdq[c] += (1.0 - beta) * lam_r * W[2][c];
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                if (s[2] < 0.0) amdq[c] += s[2] * W[2][c];
+                else            apdq[c] += s[2] * W[2][c];
+            }
+        }
+    }
+}

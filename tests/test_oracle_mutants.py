@@ -1,0 +1,90 @@
+"""Plant plausible mistakes in a copy of the CPU oracle and check that the
+oracle's pins catch every one.
+
+Each mutant is a text edit of one oracle source file (a wrong sign, a swapped
+left/right index, a dropped factor, the limiter looking downwind, ...).  The
+copy is compiled into a temporary directory and the pin suite runs against it
+in a subprocess (through ORC_LIB); the pins must fail.  Nothing here touches a
+GPU, and the real oracle sources are only read.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+# (file, original text, mutated text, what the slip is)
+MUTANTS = [
+    ("orc_acoustics.c", "double alpha2 = (dp + Z_l * du) / (Z_l + Z_r);",
+     "double alpha2 = (dp - Z_l * du) / (Z_l + Z_r);", "sign of a wave strength"),
+    ("orc_acoustics.c", "W[0][0] = -alpha1 * Z_l;", "W[0][0] = -alpha1 * Z_r;",
+     "left/right impedance swapped"),
+    ("orc_acoustics.c", "s[0] = -c_l;", "s[0] = -c_r;", "left-going speed from the wrong cell"),
+    ("orc_shallow_water.c", "double alpha2 = d2 - v_hat * d0;",
+     "double alpha2 = d2 - u_hat * d0;", "shear strength uses the normal velocity"),
+    ("orc_shallow_water.c",
+     "double u_hat = (sqh_l * u_l + sqh_r * u_r) / (sqh_l + sqh_r);",
+     "double u_hat = (sqh_r * u_l + sqh_l * u_r) / (sqh_l + sqh_r);", "Roe weights swapped"),
+    ("orc_shallow_water.c", "double beta = (lam_m - s[0]) / (lam_m - lam_l);",
+     "double beta = (s[0] - lam_l) / (lam_m - lam_l);", "entropy-fix fraction transposed"),
+    ("orc_shallow_water.c", "if (lam_l < 0.0 && 0.0 < lam_m) {",
+     "if (lam_l < 0.0 || 0.0 < lam_m) {", "entropy fix triggers off the sonic point"),
+    ("orc_shallow_water.c", "double c_hat = sqrt(g * h_bar);",
+     "double c_hat = sqrt(g * h_r);", "Roe celerity from one side"),
+    ("orc_wavesweep.c", "int J = w->s[I + 1][p] > 0.0 ? I - 1 : I + 1;",
+     "int J = w->s[I + 1][p] > 0.0 ? I + 1 : I - 1;", "limiter looks downwind"),
+    ("orc_wavesweep.c", "if (dot_ii != 0.0) phi = orc_phi(P->limiter, dot_ji / dot_ii);",
+     "if (dot_ji != 0.0) phi = orc_phi(P->limiter, dot_ii / dot_ji);", "theta ratio inverted"),
+    ("orc_wavesweep.c", "acc += as * (1.0 - nu * as) * w->Wt[I + 1][p][c];",
+     "acc += as * w->Wt[I + 1][p][c];", "dropped (1 - nu|s|) factor"),
+    ("orc_wavesweep.c", "w->F[I + 1][c] = 0.5 * acc;", "w->F[I + 1][c] = acc;",
+     "dropped 1/2 in the correction flux"),
+    ("orc_wavesweep.c", "double first = w->apdq[i + 1][c] + w->amdq[i + 2][c];",
+     "double first = w->apdq[i + 1][c] + w->amdq[i + 1][c];", "fluctuation from the wrong interface"),
+    ("orc_wavesweep.c", "double second = w->F[i + 2][c] - w->F[i + 1][c];",
+     "double second = w->F[i + 1][c] - w->F[i + 2][c];", "correction flux difference reversed"),
+    ("orc_wavesweep.c", "    *sign = -1.0;\n", "    *sign = 1.0;\n", "wall does not reflect"),
+    ("orc_wavesweep.c", "return lo ? i + N : i - N;", "return lo ? i + N : i - N + 1;",
+     "periodic wrap off by one"),
+    ("orc_wavesweep.c", "return lo ? 0 : N - 1;", "return lo ? 1 : N - 2;",
+     "extrapolation from the second cell"),
+    ("orc_wavesweep.c", "double a = 0.5 * (1.0 + theta);", "double a = (1.0 + theta);",
+     "MC centred slope without the 1/2"),
+    ("orc_wavesweep.c", "double dt = M > 0.0 ? P->cfl_desired / M : P->dt_max;",
+     "double dt = M > 0.0 ? P->cfl_max / M : P->dt_max;", "next step at cfl_max"),
+    ("orc_wavesweep.c", "        for (int d = 0; d < P->ndim; ++d) {\n            m_d[d] = orc_sweep",
+     "        for (int d = P->ndim - 1; d >= 0; --d) {\n            m_d[d] = orc_sweep",
+     "sweeps in y, x order"),
+    ("orc_wavesweep.c", "    return 2 - d;", "    return 1 + d;", "transverse momentum mapped to the normal one"),
+]
+
+
+def _build_mutant(tmp, fname, old, new):
+    src_dir = os.path.join(tmp, "src")
+    os.makedirs(src_dir, exist_ok=True)
+    for f in os.listdir(ORACLE):
+        if f.endswith((".c", ".h")):
+            shutil.copy(os.path.join(ORACLE, f), src_dir)
+    path = os.path.join(src_dir, fname)
+    text = open(path).read()
+    assert text.count(old) == 1, f"pattern not unique in {fname}: {old!r}"
+    open(path, "w").write(text.replace(old, new))
+    lib = os.path.join(tmp, "libmut.so")
+    cfiles = [os.path.join(src_dir, f) for f in sorted(os.listdir(src_dir)) if f.endswith(".c")]
+    subprocess.run(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-fopenmp",
+                    "-shared", "-o", lib] + cfiles + ["-lm"], check=True)
+    return lib
+
+
+@pytest.mark.parametrize("fname,old,new,what", MUTANTS, ids=[m[3] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, fname, old, new, what):
+    lib = _build_mutant(str(tmp_path), fname, old, new)
+    env = dict(os.environ, ORC_LIB=lib, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the mutant: {what}\n{r.stdout[-2000:]}"
