@@ -1,0 +1,289 @@
+"""Benchmark: cell-updates/s of the dimension-split wave-propagation step.
+
+Workload (default): 2D shallow water, Roe + Harten-Hyman, radial dam break on
+[-1,1]^2 at 4096 x 4096 cells, minmod, outflow boundaries, CFL 0.9, FP32
+chosen form (the FP64 plain path is timed beside it).  A step is one full
+time step: x sweep, y sweep and the device-side CFL control, over the whole
+grid.  Inputs are synthetic (seeded) and resident in HBM; each FP32 state
+version is 201 MB (> 129 MB L2), so every sweep streams from HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 4096
+METRIC = "cell-updates/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(prob, seconds_budget=20.0, max_steps=50):
+    """Time the FP64 oracle (all host threads) on full steps of the workload;
+    returns (cell-updates/s, steps, threads)."""
+    import oracle
+    o = oracle.Oracle(prob)
+    q = prob.q0
+    t0 = time.perf_counter()
+    r = o.run_steps(q, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(max_steps, int(seconds_budget / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.run_steps(r["q"], steps, dt=r["dt"])
+    el = time.perf_counter() - t0
+    return prob.ncells * steps / el, steps, oracle.threads(), el
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: each step is the full step of the
+    workload on a bounded subset of its lines (the x sweep on the first L rows
+    and the y sweep on the first L columns), so K + W steps stay within a
+    few minutes."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1805_08846_gb300 import inputs
+    prob = inputs.sw_radial_dam_break(args.n)
+    o = oracle.Oracle(prob)
+    q = prob.q0
+    dt = 0.9 / o.max_speed_over_dx(q)
+    N = args.n
+    # calibrate L: one full-size sweep pair's cost per line
+    t0 = time.perf_counter()
+    qa, _ = o.sweep(0, q, dt, 0, 64)
+    o.sweep(1, qa, dt, 0, 64)
+    per_line = (time.perf_counter() - t0) / 64
+    total_budget = 150.0
+    steps_all = args.steps + args.warmup
+    L = int(max(8, min(N, total_budget / max(steps_all * per_line, 1e-9))))
+    for _ in range(args.warmup):
+        qa, _ = o.sweep(0, q, dt, 0, L)
+        o.sweep(1, qa, dt, 0, L)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        qa, _ = o.sweep(0, q, dt, 0, L)
+        o.sweep(1, qa, dt, 0, L)
+    el = time.perf_counter() - t0
+    value = L * N * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D shallow water radial dam break {N}x{N}, Roe+HH, minmod, "
+                               f"outflow, CFL 0.9", "global_batch": 1, "seq_len": N * N},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": f"x sweep on rows [0,{L}) and y sweep on columns [0,{L}) of "
+                                   f"the {N}^2 grid per step, FP64 oracle"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path timing")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1805_08846_gb300 import Solver, inputs
+    import paper_1805_08846_gb300._lib as L
+
+    N = args.n
+    prob = inputs.sw_radial_dam_break(N)
+    ncell = prob.ncells
+    peak_gbs, peak_kind = load_peaks()
+
+    def timed(precision):
+        s = Solver.from_problem(prob, precision=precision, stream="torch")
+        s.run_steps(args.warmup)                      # warm-up: graphs, caches, clocks
+        barrier(world)
+        torch.cuda.synchronize()
+        ms, total_ms, launches = s.profile_steps(args.steps)
+        torch.cuda.synchronize()
+        barrier(world)
+        total_ms = max_over_ranks(total_ms, world)
+        q_after = None
+        s.close()
+        return ms, total_ms, launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms32, tot32, launches = timed(32)
+    clk = clocks.stop()
+    value = world * ncell * args.steps / (tot32 * 1e-3)
+
+    # Roofline of the dominant kernel: algorithmic bytes per launch =
+    # 3 fields read + 3 written, 4 B each, per cell of the grid.
+    bytes_per_launch = 6 * 4 * ncell
+    dom = 0 if ms32[0] >= ms32[1] else 1
+    achieved = bytes_per_launch / (ms32[dom] * 1e-3) / 1e9
+
+    # End to end through the public API with pinned host buffers.
+    q_host = torch.from_numpy(prob.q0).pin_memory()
+    out_host = torch.empty_like(q_host).pin_memory()
+    s = Solver.from_problem(prob, precision=32, stream="torch")
+    s.run_steps(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    s.set_q(q_host)
+    s.run_steps(args.steps)
+    s.get_q(out_host)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    s.close()
+    e2e_value = world * ncell * args.steps / e2e_s
+    state_bytes = int(q_host.numel() * 8)
+
+    fp64 = None
+    if not args.no_fp64:
+        ms64, tot64, _ = timed(64)
+        fp64 = {"value": world * ncell * args.steps / (tot64 * 1e-3), "unit": METRIC,
+                "ms_per_step": tot64 / args.steps,
+                "sweep_ms": {"x": ms64[0], "y": ms64[1]}}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot32 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"2D shallow water radial dam break {N}x{N}, Roe+HH, minmod, "
+                               f"outflow, CFL 0.9, FP32 state (FP64 dt/time)",
+                   "global_batch": world, "seq_len": ncell,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (201 MB per FP32 state version vs 129 MB L2)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "traffic": None,
+                     "kernel": f"sweep_kernel<ShallowWater<float>, minmod, dir={'xy'[dom]}>",
+                     "peak_kind": f"{peak_kind} (copy)",
+                     "sweep_ms": {"x": ms32[0], "y": ms32[1], "control": ms32[3]}},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": state_bytes / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fp64_plain": fp64,
+    }
+    if not args.no_cpu:
+        rate, steps, threads, el = cpu_oracle_rate(prob)
+        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+                                "sample": f"{steps} full FP64 oracle steps of the {N}^2 grid "
+                                          f"({el:.1f} s), {platform.machine()}"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * claw.h -- C ABI of the GB300 wave-propagation library.
+ *
+ * The library advances hyperbolic conservation laws with the dimensionally
+ * split, second-order finite-volume wave-propagation step of CUDACLAW
+ * (arXiv 1805.08846, Sec. 3, Eq. LW-update):
+ *   x sweep  Q^n -> Q*,  y sweep  Q* -> Q** (, z sweep -> Q^{n+1}),
+ * each sweep solving a Riemann problem at every interface (waves W^p,
+ * speeds s^p), forming the fluctuations A-dQ / A+dQ, limiting the waves
+ * (minmod or MC) into the correction flux F~ and applying the conservative
+ * update.  The step size follows the CFL condition (Eq. CFL-condition):
+ * the largest |s^p| / dx_d of a step decides whether the step is kept
+ * (Courant number <= cfl_max) or redone, and sets the next step to
+ * cfl_desired / max_d(max|s^p| / dx_d)  (Sec. 4.1, time-step adjustment).
+ *
+ * PDE systems (Sec. 3, Eq. acoustics and Eq. SW):
+ *   CLAW_ACOUSTICS      p_t + K div u = 0, rho u_t + grad p = 0, constant
+ *                       rho, K; 2D (m = 3: p,u,v) or 3D (m = 4: p,u,v,w);
+ *                       mwaves = 2.
+ *   CLAW_ACOUSTICS_VAR  the same with per-cell rho, K (claw_set_aux).
+ *   CLAW_SHALLOW_WATER  2D shallow water, m = 3 (h, hu, hv), mwaves = 3,
+ *                       Roe solver with the Harten-Hyman entropy fix.
+ *
+ * Conventions for every call:
+ *   - State arrays crossing the boundary are FP64, structure of arrays,
+ *     q[f][z][y][x] with x fastest, interior cells only (no ghosts),
+ *     m * nx * ny * nz doubles.  on_device = 0: a host pointer (pinned or
+ *     pageable); on_device = 1: a CUDA device pointer of the current device.
+ *     The caller keeps ownership; no pointer is retained after a call returns.
+ *   - The solver owns all of its device memory (state versions, material
+ *     arrays, control block) and a CUDA stream (the caller's, or its own
+ *     non-blocking one when the caller passes NULL).  Calls are asynchronous
+ *     on that stream except where a call says it synchronises.
+ *   - Every call returns a claw_status.  Faults found on the device (a
+ *     non-finite state, h <= 0, repeated CFL rejections, a timed-out wait)
+ *     are latched and returned by the next synchronising call.  No call
+ *     aborts the process and none waits without bound.
+ *   - claw_last_error() returns a thread-local message for the last failure.
+ *   - Precision: claw_params.precision = 64 keeps state and arithmetic in
+ *     FP64; 32 keeps the state and the Riemann / limiter / update arithmetic
+ *     in FP32, with the time step, simulated time and conservation sums in
+ *     FP64 in both cases.
+ */
+#ifndef CLAW_H
+#define CLAW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct claw_solver claw_solver;   /* opaque; owns all device memory */
+
+typedef enum {
+    CLAW_OK = 0,
+    CLAW_EINVAL = 1,     /* bad argument; nothing was changed */
+    CLAW_ENOMEM = 2,     /* device or pinned host allocation failed */
+    CLAW_ECUDA = 3,      /* a CUDA runtime call failed (message in claw_last_error) */
+    CLAW_ECFL = 4,       /* more than max_retries consecutive CFL rejections */
+    CLAW_ENONPHYS = 5,   /* NaN / Inf in the state, or h <= 0 (shallow water) */
+    CLAW_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    CLAW_EBOUNDS = 7     /* a size or index outside the supported range */
+} claw_status;
+
+typedef enum { CLAW_BC_PERIODIC = 0, CLAW_BC_EXTRAP = 1, CLAW_BC_WALL = 2 } claw_bc;
+typedef enum { CLAW_ACOUSTICS = 0, CLAW_ACOUSTICS_VAR = 1, CLAW_SHALLOW_WATER = 2 } claw_system;
+typedef enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_MC = 2 } claw_limiter;
+
+/* Grid of one problem: ndim = 2 or 3; n[d] interior cells (>= 2 in each
+ * used direction; n[2] is ignored in 2D); dx[d] > 0 cell widths. */
+typedef struct { int ndim; int n[3]; double dx[3]; } claw_grid;
+
+/* rho, K: constant acoustics coefficients (also the initial per-cell values
+ * of CLAW_ACOUSTICS_VAR); g: gravity; cfl_desired: Courant number the next
+ * step aims at; cfl_max: a step above it is redone; dt_max: cap on dt;
+ * precision: 32 or 64; max_retries: consecutive rejections before
+ * CLAW_ECFL (<= 0 selects 8). */
+typedef struct {
+    double rho, K, g;
+    double cfl_desired, cfl_max, dt_max;
+    int precision;
+    int max_retries;
+} claw_params;
+
+/* Ghost cells, two per side, filled inside each sweep from the state it is
+ * about to read (Sec. 4.1 boundary stage): bc[2d] is the low side of
+ * direction d, bc[2d+1] the high side.  PERIODIC wraps; EXTRAP copies the
+ * edge cell; WALL mirrors the two edge cells and negates the normal
+ * velocity / momentum.  Material coefficients follow the same index rule. */
+
+/* ---------------------------------------------------------------- single grid */
+
+/* Create a solver for one grid.  (m, mwaves) must match the system:
+ * (3,2) 2D acoustics, (4,2) 3D acoustics, (3,3) shallow water (2D only);
+ * otherwise CLAW_EINVAL.  cuda_stream: a cudaStream_t (e.g. a torch stream)
+ * or NULL.  The state starts at zero (h = 1 for shallow water), t = 0. */
+claw_status claw_create(const claw_grid* grid, int m, int mwaves, claw_system system,
+                        claw_limiter limiter, const claw_bc bc[6], const claw_params* params,
+                        void* cuda_stream, claw_solver** out);
+
+/* Release every resource of the solver (synchronises its stream).  NULL is a no-op. */
+void claw_destroy(claw_solver* s);
+
+/* Copy a new state in (FP64 SoA, see conventions) and set the next step from
+ * a speeds-only Riemann pass over it: dt = cfl_desired / max_d(m_d / dx_d). */
+claw_status claw_set_q(claw_solver* s, const double* q_soa, int on_device);
+
+/* Copy the current state out (FP64 SoA).  Synchronises; returns any latched
+ * device fault. */
+claw_status claw_get_q(claw_solver* s, double* q_soa, int on_device);
+
+/* Per-cell rho and K (nx*ny*nz doubles each, x fastest) for
+ * CLAW_ACOUSTICS_VAR; impedance Z = rho c and c = sqrt(K / rho) are formed
+ * once per cell, in FP64.  CLAW_EINVAL for other systems or rho, K <= 0 is
+ * not checked (the caller guarantees positivity). */
+claw_status claw_set_aux(claw_solver* s, const double* rho, const double* K, int on_device);
+
+/* One accepted step.  dt > 0: exactly that step, always kept (no CFL
+ * control); dt <= 0: the CFL rule, redone on a violation.  *cfl_out (may be
+ * NULL) receives the Courant number of the kept step.  Synchronises. */
+claw_status claw_step(claw_solver* s, double dt, double* cfl_out);
+
+/* Advance to t_final (>= current t, else CLAW_EINVAL) under the CFL rule;
+ * the last step is shortened to land on t_final exactly.  cfl_target > 0
+ * replaces cfl_desired.  *nsteps_out (may be NULL) gets the accepted steps.
+ * Runs as CUDA graphs of several steps with the step control on the device.
+ * Synchronises. */
+claw_status claw_advance(claw_solver* s, double t_final, double cfl_target, int* nsteps_out);
+
+/* Take nsteps accepted steps under the CFL rule (rejected attempts are
+ * redone and not counted), as CUDA graphs.  Synchronises. */
+claw_status claw_run_steps(claw_solver* s, int nsteps);
+
+/* max_d (max|s^p| / dx_d) of the current state, in FP64.  Synchronises. */
+claw_status claw_max_speed(claw_solver* s, double* smax_over_dx);
+
+/* Simulated time, next step, accepted steps.  Synchronises. */
+claw_status claw_get_time(claw_solver* s, double* t, double* dt, long* nsteps);
+
+/* Restore the clock (checkpoint / resume).  dt <= 0 recomputes the next
+ * step from the current state. */
+claw_status claw_set_time(claw_solver* s, double t, double dt, long nsteps);
+
+/* Sum of each field over the interior cells (m doubles), accumulated in
+ * FP64 in a fixed order (deterministic).  Synchronises. */
+claw_status claw_conservation_sums(claw_solver* s, double* sums);
+
+/* Rejected attempts so far.  Synchronises. */
+claw_status claw_get_rejections(claw_solver* s, long* nrej);
+
+/* Thread-local text of the last failure ("" if none). */
+const char* claw_last_error(void);
+
+/* ---------------------------------------------------------------- ensembles */
+
+/* B >= 1 independent problems of one system and limiter, each with its own
+ * grid (all of the same ndim), time, step size and CFL control, advanced
+ * together: one launch per sweep covers the tiles of every instance.
+ * m and mwaves follow from the system; bc applies to every instance. */
+claw_status claw_ensemble_create(int B, const claw_grid* grids, claw_system system,
+                                 claw_limiter limiter, const claw_bc bc[6],
+                                 const claw_params* params, void* cuda_stream,
+                                 claw_solver** out);
+claw_status claw_ensemble_set_q(claw_solver* s, int i, const double* q, int on_device);
+claw_status claw_ensemble_get_q(claw_solver* s, int i, double* q, int on_device);
+claw_status claw_ensemble_set_aux(claw_solver* s, int i, const double* rho, const double* K,
+                                  int on_device);
+/* nsteps accepted steps for every instance, each under its own CFL rule. */
+claw_status claw_ensemble_run_steps(claw_solver* s, int nsteps);
+claw_status claw_ensemble_get_time(claw_solver* s, int i, double* t, double* dt, long* nsteps);
+int         claw_ensemble_size(const claw_solver* s);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Take nsteps accepted steps like claw_run_steps inside one CUDA graph whose
+ * kernels are bracketed by CUDA events, and report the average duration of
+ * one launch of each kernel kind: kernel_ms[d] for the d-sweep (d < ndim),
+ * kernel_ms[3] for the step-control kernel; *total_ms for the whole graph.
+ * *launches receives the number of kernels launched.  Synchronises. */
+claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
+                               double* total_ms, long* launches);
+
+/* Tuning knobs (the autotuner drives these): cells per line segment of one
+ * thread in direction d (>= 4). Rebuilds the tile lists. */
+claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLAW_H */

@@ -1,0 +1,677 @@
+// Host side of the C ABI declared in include/claw.h: argument checks, device
+// memory, tile lists, CUDA graphs of step attempts, and status reporting.
+#include <claw.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+using namespace claw;
+
+namespace {
+
+thread_local std::string g_err;
+
+claw_status fail(claw_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+claw_status fail(claw_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? CLAW_ENOMEM : CLAW_ECUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKS(expr)                          \
+    do {                                   \
+        claw_status s_ = (expr);           \
+        if (s_ != CLAW_OK) return s_;      \
+    } while (0)
+
+int slot_of_version(int v) { return v == 0 ? 0 : 1 + (v - 1) % 2; }
+
+// Fields a sweep along d changes (the reduced state of the Riemann solver).
+std::vector<int> touched_fields(int system, int d) {
+    if (system == kSysShallowWater) return {0, 1, 2};
+    return {0, 1 + d};
+}
+
+}  // namespace
+
+struct claw_solver {
+    int B = 0, ndim = 0, m = 0, mwaves = 0, system = 0, limiter = 0, precision = 64;
+    size_t esize = 8;
+    claw_params params{};
+    int bc[6]{};
+    std::vector<InstDesc> inst;
+    InstDesc* d_inst = nullptr;
+    Control* d_ctl = nullptr;
+    Control* h_ctl = nullptr;  // pinned mirror for reads
+    void* pool = nullptr;
+    void* aux = nullptr;
+    double* stage = nullptr;
+    double* d_sums = nullptr;
+    size_t stage_elems = 0;
+    int seg[3] = {64, 64, 64};
+    std::vector<TileDesc> tiles[3];
+    TileDesc* d_tiles[3] = {nullptr, nullptr, nullptr};
+    std::vector<std::pair<int, int>> inst_tiles[3];  // [lo, hi) tile range per instance
+    SlotMap slots[3]{};
+    FinalSlots fin{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<int, cudaGraphExec_t> graphs;
+    double Z = 0, c = 0;
+};
+
+namespace {
+
+claw_status check_grid(const claw_grid* g, int ndim_expect) {
+    if (!g) return fail(CLAW_EINVAL, "grid is NULL");
+    if (g->ndim != 2 && g->ndim != 3) return fail(CLAW_EINVAL, "ndim must be 2 or 3 (got %d)", g->ndim);
+    if (ndim_expect && g->ndim != ndim_expect)
+        return fail(CLAW_EINVAL, "all ensemble grids must share ndim");
+    long long cells = 1;
+    for (int d = 0; d < g->ndim; ++d) {
+        if (g->n[d] < 2) return fail(CLAW_EINVAL, "n[%d] = %d: need at least 2 cells", d, g->n[d]);
+        if (g->n[d] > (1 << 24)) return fail(CLAW_EBOUNDS, "n[%d] = %d too large", d, g->n[d]);
+        if (!(g->dx[d] > 0.0)) return fail(CLAW_EINVAL, "dx[%d] must be > 0", d);
+        cells *= g->n[d];
+    }
+    if (cells > (1ll << 34)) return fail(CLAW_EBOUNDS, "grid of %lld cells too large", cells);
+    return CLAW_OK;
+}
+
+claw_status free_graphs(claw_solver* s) {
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    return CLAW_OK;
+}
+
+claw_status build_tiles(claw_solver* s) {
+    free_graphs(s);
+    for (int d = 0; d < s->ndim; ++d) {
+        auto& T = s->tiles[d];
+        T.clear();
+        s->inst_tiles[d].assign(s->B, {0, 0});
+        const int L = s->seg[d];
+        for (int i = 0; i < s->B; ++i) {
+            const InstDesc& I = s->inst[i];
+            const int lo = (int)T.size();
+            const int N = I.n[d];
+            if (d == 0) {
+                const int rows = I.n[1] * I.n[2];
+                for (int r0 = 0; r0 < rows; r0 += kLines)
+                    for (int a = 0; a < N; a += L) T.push_back({i, r0, 0, a, std::min(a + L, N), {0, 0, 0}});
+            } else {
+                const int others = (d == 1) ? I.n[2] : I.n[1];
+                for (int o = 0; o < others; ++o)
+                    for (int x0 = 0; x0 < I.n[0]; x0 += kLines)
+                        for (int a = 0; a < N; a += L) T.push_back({i, x0, o, a, std::min(a + L, N), {0, 0, 0}});
+            }
+            s->inst_tiles[d][i] = {lo, (int)T.size()};
+        }
+        if (s->d_tiles[d]) cudaFree(s->d_tiles[d]);
+        s->d_tiles[d] = nullptr;
+        CK(cudaMalloc(&s->d_tiles[d], sizeof(TileDesc) * std::max<size_t>(T.size(), 1)));
+        CK(cudaMemcpy(s->d_tiles[d], T.data(), sizeof(TileDesc) * T.size(), cudaMemcpyHostToDevice));
+    }
+    return CLAW_OK;
+}
+
+SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi) {
+    SweepArgs a{};
+    a.tiles = s->d_tiles[d] + tile_lo;
+    a.ntiles = tile_hi - tile_lo;
+    a.inst = s->d_inst;
+    a.ctl = s->d_ctl;
+    a.pool = s->pool;
+    a.aux = s->aux;
+    a.inst_lo = 0;
+    a.inst_hi = s->B;
+    a.slots = s->slots[d];
+    a.Z = s->Z;
+    a.c = s->c;
+    a.g = s->params.g;
+    return a;
+}
+
+claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, bool speeds) {
+    SweepLaunch L{};
+    L.args = sweep_args(s, d, tile_lo, tile_hi);
+    L.system = s->system;
+    L.limiter = s->limiter;
+    L.dir = d;
+    L.precision = s->precision;
+    L.speeds = speeds;
+    L.grid = (unsigned)(tile_hi - tile_lo);
+    L.stream = s->stream;
+    CK(launch_sweep(L));
+    return CLAW_OK;
+}
+
+// One step attempt for every instance: the sweeps in x, y(, z) order, then
+// the step-control kernel.
+claw_status enqueue_attempt(claw_solver* s) {
+    for (int d = 0; d < s->ndim; ++d) CKS(launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false));
+    CK(launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->stream));
+    return CLAW_OK;
+}
+
+claw_status get_graph(claw_solver* s, int K, cudaGraphExec_t* out) {
+    auto it = s->graphs.find(K);
+    if (it != s->graphs.end()) {
+        *out = it->second;
+        return CLAW_OK;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    claw_status st = CLAW_OK;
+    for (int k = 0; k < K && st == CLAW_OK; ++k) st = enqueue_attempt(s);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (st != CLAW_OK) return st;
+    CK(e);
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    s->graphs[K] = ex;
+    *out = ex;
+    return CLAW_OK;
+}
+
+claw_status read_ctl(claw_solver* s) {
+    CK(cudaMemcpyAsync(s->h_ctl, s->d_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CLAW_OK;
+}
+
+claw_status status_of(unsigned bits) {
+    if (bits & kStatNonPhys) return fail(CLAW_ENONPHYS, "non-finite state or h <= 0 detected on the device");
+    if (bits & kStatCfl) return fail(CLAW_ECFL, "too many consecutive CFL rejections");
+    if (bits & kStatTimeout) return fail(CLAW_ETIMEOUT, "a device-side wait timed out");
+    if (bits & kStatBounds) return fail(CLAW_EBOUNDS, "device-side bounds check failed");
+    return CLAW_OK;
+}
+
+claw_status latched_status(claw_solver* s, int lo, int hi) {
+    unsigned bits = 0;
+    for (int i = lo; i < hi; ++i) bits |= s->h_ctl[i].status;
+    return status_of(bits);
+}
+
+// Replay graphs of step attempts until every instance reached its target
+// (kModeSteps) or t_final (kModeTFinal), or latched a fault.
+claw_status run_armed(claw_solver* s, int mode, long long nsteps) {
+    long long budget;   // attempts, bounded
+    int K;
+    if (mode == kModeSteps) {
+        long long remaining = nsteps;
+        while (remaining > 0) {
+            K = (int)std::min<long long>(remaining, 512);
+            cudaGraphExec_t ex;
+            CKS(get_graph(s, K, &ex));
+            CK(cudaGraphLaunch(ex, s->stream));
+            remaining -= K;
+        }
+        budget = 64 + 16ll * (s->params.max_retries + 1) * std::max<long long>(nsteps, 1);
+        for (;;) {
+            CKS(read_ctl(s));
+            long long deficit = 0;
+            for (int i = 0; i < s->B; ++i)
+                if (!s->h_ctl[i].status && s->h_ctl[i].active)
+                    deficit = std::max(deficit, s->h_ctl[i].target - s->h_ctl[i].nacc);
+            if (deficit <= 0) break;
+            if ((budget -= deficit) < 0) return fail(CLAW_ETIMEOUT, "step attempts exceeded their bound");
+            K = (int)std::min<long long>(deficit, 512);
+            cudaGraphExec_t ex;
+            CKS(get_graph(s, K, &ex));
+            CK(cudaGraphLaunch(ex, s->stream));
+        }
+    } else {
+        budget = 1ll << 24;
+        K = 16;
+        for (;;) {
+            cudaGraphExec_t ex;
+            CKS(get_graph(s, K, &ex));
+            CK(cudaGraphLaunch(ex, s->stream));
+            CKS(read_ctl(s));
+            bool any = false;
+            for (int i = 0; i < s->B; ++i) any |= (!s->h_ctl[i].status && s->h_ctl[i].active);
+            if (!any) break;
+            if ((budget -= K) < 0) return fail(CLAW_ETIMEOUT, "step attempts exceeded their bound");
+            K = std::min(K * 2, 256);
+        }
+    }
+    return latched_status(s, 0, s->B);
+}
+
+claw_status speed_pass(claw_solver* s, int i, int set_dt) {
+    for (int d = 0; d < s->ndim; ++d) {
+        auto r = s->inst_tiles[d][i];
+        CKS(launch_sweep_range(s, d, r.first, r.second, true));
+    }
+    CK(launch_speed_reduce(s->d_ctl, s->d_inst, i, i + 1, set_dt, s->stream));
+    return CLAW_OK;
+}
+
+claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_system system,
+                        claw_limiter limiter, const claw_bc bc[6], const claw_params* params,
+                        void* stream, claw_solver** out) {
+    if (!out) return fail(CLAW_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
+    if (!grids || !bc || !params) return fail(CLAW_EINVAL, "NULL argument");
+    if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
+    if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_MC) return fail(CLAW_EINVAL, "unknown limiter %d", (int)limiter);
+    const int ndim = grids[0].ndim;
+    for (int i = 0; i < B; ++i) CKS(check_grid(&grids[i], ndim));
+    if (system == CLAW_SHALLOW_WATER && ndim != 2) return fail(CLAW_EINVAL, "shallow water is 2D only");
+    const int m_exp = system == CLAW_SHALLOW_WATER ? 3 : ndim + 1;
+    const int mw_exp = system == CLAW_SHALLOW_WATER ? 3 : 2;
+    if (m != m_exp || mwaves != mw_exp)
+        return fail(CLAW_EINVAL, "(m, mwaves) = (%d, %d) does not match the system (expected (%d, %d))", m, mwaves, m_exp, mw_exp);
+    for (int k = 0; k < 2 * ndim; ++k)
+        if (bc[k] < CLAW_BC_PERIODIC || bc[k] > CLAW_BC_WALL) return fail(CLAW_EINVAL, "unknown bc[%d] = %d", k, (int)bc[k]);
+    if (params->precision != 32 && params->precision != 64) return fail(CLAW_EINVAL, "precision must be 32 or 64");
+    if (!(params->cfl_desired > 0.0) || !(params->cfl_max > 0.0)) return fail(CLAW_EINVAL, "cfl_desired and cfl_max must be > 0");
+    if (!(params->dt_max > 0.0)) return fail(CLAW_EINVAL, "dt_max must be > 0");
+    if (system != CLAW_SHALLOW_WATER && (!(params->rho > 0.0) || !(params->K > 0.0)))
+        return fail(CLAW_EINVAL, "rho and K must be > 0");
+    if (system == CLAW_SHALLOW_WATER && !(params->g > 0.0)) return fail(CLAW_EINVAL, "g must be > 0");
+
+    claw_solver* s = new claw_solver();
+    s->B = B;
+    s->ndim = ndim;
+    s->m = m;
+    s->mwaves = mwaves;
+    s->system = system;
+    s->limiter = limiter;
+    s->precision = params->precision;
+    s->esize = params->precision == 64 ? 8 : 4;
+    s->params = *params;
+    if (s->params.max_retries <= 0) s->params.max_retries = 8;
+    for (int k = 0; k < 6; ++k) s->bc[k] = (k < 2 * ndim) ? bc[k] : CLAW_BC_EXTRAP;
+    s->c = std::sqrt(params->K / params->rho);
+    s->Z = params->rho * s->c;
+    *out = s;   // from here on failures clean up through claw_destroy
+
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        s->own_stream = true;
+    }
+
+    // Storage layout.
+    long long off = 0, aux_off = 0;
+    size_t max_cells = 0;
+    s->inst.resize(B);
+    for (int i = 0; i < B; ++i) {
+        InstDesc& I = s->inst[i];
+        memset(&I, 0, sizeof I);
+        I.ndim = ndim;
+        for (int d = 0; d < 3; ++d) {
+            I.n[d] = d < ndim ? grids[i].n[d] : 1;
+            I.dx[d] = d < ndim ? grids[i].dx[d] : 1.0;
+        }
+        I.pitch = (I.n[0] + 31) / 32 * 32;
+        I.fstride = (long long)I.n[2] * I.n[1] * I.pitch;
+        I.vstride = (long long)m * I.fstride;
+        I.offset = off;
+        off += 3 * I.vstride;
+        off = (off + 63) / 64 * 64;
+        if (system == CLAW_ACOUSTICS_VAR) {
+            I.aux_offset = aux_off;
+            aux_off += 2 * I.fstride;
+            aux_off = (aux_off + 63) / 64 * 64;
+        } else {
+            I.aux_offset = -1;
+        }
+        for (int k = 0; k < 6; ++k) I.bc[k] = s->bc[k];
+        max_cells = std::max(max_cells, (size_t)I.n[0] * I.n[1] * I.n[2]);
+    }
+    CK(cudaMalloc(&s->pool, (size_t)off * s->esize));
+    CK(cudaMemsetAsync(s->pool, 0, (size_t)off * s->esize, s->stream));
+    if (aux_off) CK(cudaMalloc(&s->aux, (size_t)aux_off * s->esize));
+    s->stage_elems = max_cells * m;
+    CK(cudaMalloc(&s->stage, s->stage_elems * sizeof(double)));
+    CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
+    CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
+    CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
+
+    std::vector<Control> ctl(B);
+    for (int i = 0; i < B; ++i) {
+        Control& c = ctl[i];
+        memset(&c, 0, sizeof c);
+        c.cfl_desired = params->cfl_desired;
+        c.cfl_max = params->cfl_max;
+        c.dt_max = params->dt_max;
+        c.max_retries = s->params.max_retries;
+        c.mode = kModeIdle;
+    }
+    CK(cudaMalloc(&s->d_ctl, sizeof(Control) * B));
+    CK(cudaMemcpyAsync(s->d_ctl, ctl.data(), sizeof(Control) * B, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMallocHost(&s->h_ctl, sizeof(Control) * B));
+
+    // Version slots: each sweep reads a field's latest version of the step
+    // and writes the next one; a field's versions cycle through 3 slots.
+    int ver[4] = {0, 0, 0, 0};
+    for (int d = 0; d < ndim; ++d) {
+        memset(&s->slots[d], 0, sizeof(SlotMap));
+        for (int f : touched_fields(system, d)) {
+            s->slots[d].in_off[f] = (signed char)slot_of_version(ver[f]);
+            s->slots[d].out_off[f] = (signed char)slot_of_version(ver[f] + 1);
+            ver[f] += 1;
+        }
+    }
+    s->fin.m = m;
+    for (int f = 0; f < 4; ++f) s->fin.off[f] = slot_of_version(ver[f]);
+
+    CKS(build_tiles(s));
+    // Initial state: zero (h = 1 for shallow water); material from params.
+    for (int i = 0; i < B; ++i) {
+        if (system == CLAW_SHALLOW_WATER) CK(launch_fill(s->precision, s->pool, s->inst[i], 0, 0, 1.0, s->stream));
+        if (system == CLAW_ACOUSTICS_VAR)
+            CK(launch_aux_const(s->precision, s->aux, s->inst[i], params->rho, params->K, s->stream));
+        CKS(speed_pass(s, i, 1));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return CLAW_OK;
+}
+
+claw_status check_solver(claw_solver* s, int i = 0) {
+    if (!s) return fail(CLAW_EINVAL, "solver is NULL");
+    if (i < 0 || i >= s->B) return fail(CLAW_EINVAL, "instance %d out of range [0, %d)", i, s->B);
+    return CLAW_OK;
+}
+
+claw_status set_q_impl(claw_solver* s, int i, const double* q, int on_device) {
+    CKS(check_solver(s, i));
+    if (!q) return fail(CLAW_EINVAL, "q is NULL");
+    const InstDesc& I = s->inst[i];
+    const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2] * s->m;
+    const double* src = q;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(s->stage, q, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        src = s->stage;
+    }
+    CK(launch_reset_status(s->d_ctl, i, s->stream));
+    CK(launch_convert_in(s->precision, s->pool, I, s->d_ctl + i, src, s->m, s->stream));
+    CKS(speed_pass(s, i, 1));
+    if (!on_device) CK(cudaStreamSynchronize(s->stream));   // the host buffer may go away
+    return CLAW_OK;
+}
+
+claw_status get_q_impl(claw_solver* s, int i, double* q, int on_device) {
+    CKS(check_solver(s, i));
+    if (!q) return fail(CLAW_EINVAL, "q is NULL");
+    const InstDesc& I = s->inst[i];
+    const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2] * s->m;
+    double* dst = on_device ? q : s->stage;
+    CK(launch_convert_out(s->precision, s->pool, I, s->d_ctl + i, dst, s->m, s->stream));
+    if (!on_device) CK(cudaMemcpyAsync(q, s->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CKS(read_ctl(s));
+    return latched_status(s, i, i + 1);
+}
+
+claw_status set_aux_impl(claw_solver* s, int i, const double* rho, const double* K, int on_device) {
+    CKS(check_solver(s, i));
+    if (s->system != CLAW_ACOUSTICS_VAR) return fail(CLAW_EINVAL, "claw_set_aux needs CLAW_ACOUSTICS_VAR");
+    if (!rho || !K) return fail(CLAW_EINVAL, "rho or K is NULL");
+    const InstDesc& I = s->inst[i];
+    const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2];
+    const double *r = rho, *k = K;
+    if (!on_device) {
+        // the stage holds m >= 2 fields' worth of doubles
+        CK(cudaMemcpyAsync(s->stage, rho, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->stage + n, K, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        r = s->stage;
+        k = s->stage + n;
+    }
+    CK(launch_aux(s->precision, s->aux, I, r, k, s->stream));
+    CKS(speed_pass(s, i, 1));
+    CK(cudaStreamSynchronize(s->stream));
+    return CLAW_OK;
+}
+
+}  // namespace
+
+cudaError_t claw::launch_sweep(const SweepLaunch& L) {
+    switch (L.system) {
+        case kSysAcoustics:
+            return L.precision == 64 ? launch_sweep_acoustics_f64(L) : launch_sweep_acoustics_f32(L);
+        case kSysAcousticsVar:
+            return L.precision == 64 ? launch_sweep_acoustics_var_f64(L) : launch_sweep_acoustics_var_f32(L);
+        default:
+            return L.precision == 64 ? launch_sweep_shallow_water_f64(L) : launch_sweep_shallow_water_f32(L);
+    }
+}
+
+extern "C" {
+
+const char* claw_last_error(void) { return g_err.c_str(); }
+
+claw_status claw_create(const claw_grid* grid, int m, int mwaves, claw_system system,
+                        claw_limiter limiter, const claw_bc bc[6], const claw_params* params,
+                        void* cuda_stream, claw_solver** out) {
+    claw_status st = create_impl(1, grid, m, mwaves, system, limiter, bc, params, cuda_stream, out);
+    if (st != CLAW_OK && out && *out) {
+        std::string keep = g_err;
+        claw_destroy(*out);
+        *out = nullptr;
+        g_err = keep;
+    }
+    return st;
+}
+
+claw_status claw_ensemble_create(int B, const claw_grid* grids, claw_system system,
+                                 claw_limiter limiter, const claw_bc bc[6],
+                                 const claw_params* params, void* cuda_stream, claw_solver** out) {
+    if (!grids) return fail(CLAW_EINVAL, "grids is NULL");
+    if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
+    const int ndim = grids[0].ndim;
+    const int m = system == CLAW_SHALLOW_WATER ? 3 : ndim + 1;
+    const int mw = system == CLAW_SHALLOW_WATER ? 3 : 2;
+    claw_status st = create_impl(B, grids, m, mw, system, limiter, bc, params, cuda_stream, out);
+    if (st != CLAW_OK && out && *out) {
+        std::string keep = g_err;
+        claw_destroy(*out);
+        *out = nullptr;
+        g_err = keep;
+    }
+    return st;
+}
+
+void claw_destroy(claw_solver* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_graphs(s);
+    for (int d = 0; d < 3; ++d)
+        if (s->d_tiles[d]) cudaFree(s->d_tiles[d]);
+    if (s->pool) cudaFree(s->pool);
+    if (s->aux) cudaFree(s->aux);
+    if (s->stage) cudaFree(s->stage);
+    if (s->d_sums) cudaFree(s->d_sums);
+    if (s->d_inst) cudaFree(s->d_inst);
+    if (s->d_ctl) cudaFree(s->d_ctl);
+    if (s->h_ctl) cudaFreeHost(s->h_ctl);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+claw_status claw_set_q(claw_solver* s, const double* q, int on_device) { return set_q_impl(s, 0, q, on_device); }
+claw_status claw_get_q(claw_solver* s, double* q, int on_device) { return get_q_impl(s, 0, q, on_device); }
+claw_status claw_set_aux(claw_solver* s, const double* rho, const double* K, int on_device) {
+    return set_aux_impl(s, 0, rho, K, on_device);
+}
+claw_status claw_ensemble_set_q(claw_solver* s, int i, const double* q, int on_device) {
+    return set_q_impl(s, i, q, on_device);
+}
+claw_status claw_ensemble_get_q(claw_solver* s, int i, double* q, int on_device) {
+    return get_q_impl(s, i, q, on_device);
+}
+claw_status claw_ensemble_set_aux(claw_solver* s, int i, const double* rho, const double* K, int on_device) {
+    return set_aux_impl(s, i, rho, K, on_device);
+}
+int claw_ensemble_size(const claw_solver* s) { return s ? s->B : 0; }
+
+claw_status claw_step(claw_solver* s, double dt, double* cfl_out) {
+    CKS(check_solver(s));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, 1, 0.0, dt > 0.0 ? dt : 0.0, 0.0, s->stream));
+    CKS(run_armed(s, kModeSteps, 1));
+    if (cfl_out) *cfl_out = s->h_ctl[0].cfl_last;
+    return CLAW_OK;
+}
+
+claw_status claw_run_steps(claw_solver* s, int nsteps) {
+    CKS(check_solver(s));
+    if (nsteps < 0) return fail(CLAW_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return CLAW_OK;
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->stream));
+    return run_armed(s, kModeSteps, nsteps);
+}
+
+claw_status claw_ensemble_run_steps(claw_solver* s, int nsteps) { return claw_run_steps(s, nsteps); }
+
+claw_status claw_advance(claw_solver* s, double t_final, double cfl_target, int* nsteps_out) {
+    CKS(check_solver(s));
+    CKS(read_ctl(s));
+    const double t0 = s->h_ctl[0].t;
+    const long long n0 = s->h_ctl[0].nacc;
+    if (!(t_final >= t0)) return fail(CLAW_EINVAL, "t_final %.17g is before the current time %.17g", t_final, t0);
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeTFinal, 0, t_final, 0.0, cfl_target > 0.0 ? cfl_target : 0.0, s->stream));
+    claw_status st = run_armed(s, kModeTFinal, 0);
+    if (nsteps_out) *nsteps_out = (int)(s->h_ctl[0].nacc - n0);
+    return st;
+}
+
+claw_status claw_max_speed(claw_solver* s, double* smax_over_dx) {
+    CKS(check_solver(s));
+    if (!smax_over_dx) return fail(CLAW_EINVAL, "output is NULL");
+    CKS(speed_pass(s, 0, 0));
+    CKS(read_ctl(s));
+    *smax_over_dx = s->h_ctl[0].M_last;
+    return latched_status(s, 0, 1);
+}
+
+claw_status claw_ensemble_get_time(claw_solver* s, int i, double* t, double* dt, long* nsteps) {
+    CKS(check_solver(s, i));
+    CKS(read_ctl(s));
+    if (t) *t = s->h_ctl[i].t;
+    if (dt) *dt = s->h_ctl[i].dt;
+    if (nsteps) *nsteps = (long)s->h_ctl[i].nacc;
+    return latched_status(s, i, i + 1);
+}
+
+claw_status claw_get_time(claw_solver* s, double* t, double* dt, long* nsteps) {
+    return claw_ensemble_get_time(s, 0, t, dt, nsteps);
+}
+
+claw_status claw_get_rejections(claw_solver* s, long* nrej) {
+    CKS(check_solver(s));
+    CKS(read_ctl(s));
+    long tot = 0;
+    for (int i = 0; i < s->B; ++i) tot += (long)s->h_ctl[i].nrej;
+    if (nrej) *nrej = tot;
+    return latched_status(s, 0, s->B);
+}
+
+claw_status claw_set_time(claw_solver* s, double t, double dt, long nsteps) {
+    CKS(check_solver(s));
+    if (nsteps < 0) return fail(CLAW_EINVAL, "nsteps < 0");
+    CK(launch_set_time(s->d_ctl, 0, t, dt, nsteps, s->stream));
+    if (!(dt > 0.0)) CKS(speed_pass(s, 0, 1));
+    CK(cudaStreamSynchronize(s->stream));
+    return CLAW_OK;
+}
+
+claw_status claw_conservation_sums(claw_solver* s, double* sums) {
+    CKS(check_solver(s));
+    if (!sums) return fail(CLAW_EINVAL, "sums is NULL");
+    CK(launch_sums(s->precision, s->pool, s->inst[0], s->d_ctl, s->m, s->d_sums, s->stream));
+    CK(cudaMemcpyAsync(sums, s->d_sums, sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+    CKS(read_ctl(s));
+    return latched_status(s, 0, 1);
+}
+
+claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
+    CKS(check_solver(s));
+    if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
+    if (seg_len < 4) return fail(CLAW_EINVAL, "segment length must be >= 4");
+    CK(cudaStreamSynchronize(s->stream));
+    s->seg[d] = seg_len;
+    return build_tiles(s);
+}
+
+claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], double* total_ms,
+                               long* launches) {
+    CKS(check_solver(s));
+    if (nsteps < 1) return fail(CLAW_EINVAL, "nsteps must be >= 1");
+    const int nk = s->ndim + 1;
+    std::vector<cudaEvent_t> ev((size_t)nsteps * nk * 2);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->stream));
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    claw_status st = CLAW_OK;
+    for (int k = 0; k < nsteps && st == CLAW_OK; ++k) {
+        for (int d = 0; d <= s->ndim && st == CLAW_OK; ++d) {
+            cudaEvent_t* e = &ev[((size_t)k * nk + d) * 2];
+            cudaEventRecord(e[0], s->stream);
+            if (d < s->ndim) st = launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false);
+            else if (launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->stream) != cudaSuccess)
+                st = fail(CLAW_ECUDA, "finish launch failed");
+            cudaEventRecord(e[1], s->stream);
+        }
+    }
+    cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
+    if (st != CLAW_OK) return st;
+    CK(ce);
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    CK(cudaEventRecord(t0, s->stream));
+    CK(cudaGraphLaunch(ex, s->stream));
+    CK(cudaEventRecord(t1, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nsteps; ++k)
+        for (int d = 0; d <= s->ndim; ++d) {
+            float ms = 0.f;
+            cudaEvent_t* e = &ev[((size_t)k * nk + d) * 2];
+            CK(cudaEventElapsedTime(&ms, e[0], e[1]));
+            acc[d < s->ndim ? d : 3] += ms;
+        }
+    float tot = 0.f;
+    CK(cudaEventElapsedTime(&tot, t0, t1));
+    for (int d = 0; d < 4; ++d) kernel_ms[d] = acc[d] / nsteps;
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (long)nsteps * nk;
+    cudaGraphExecDestroy(ex);
+    for (auto& e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    CKS(read_ctl(s));
+    return latched_status(s, 0, s->B);
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Device/host data structures shared by the sweep kernels, the step-control
+// kernels and the host API of the wave-propagation library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace claw {
+
+// Threads (one grid line each) per tile / CTA of a sweep.
+constexpr int kLines = 128;
+
+// Status bits latched on the device and reported by synchronising calls.
+enum : unsigned {
+    kStatNonPhys = 1u,   // NaN / Inf in the state or h <= 0
+    kStatCfl = 2u,       // too many consecutive CFL rejections
+    kStatTimeout = 4u,   // a bounded wait gave up
+    kStatBounds = 8u,    // an index check failed
+};
+
+// Step-control modes (Control::mode).
+enum : int { kModeIdle = 0, kModeSteps = 1, kModeTFinal = 2 };
+
+// Geometry and storage of one instance (one grid).  State storage is three
+// version slots of m field planes each: element (slot, f, z, y, x) lives at
+//   offset + slot * vstride + f * fstride + (z * ny + y) * pitch + x.
+struct InstDesc {
+    int n[3];              // interior cells nx, ny, nz (nz = 1 in 2D)
+    int pitch;             // row pitch in elements (multiple of 32)
+    long long fstride;     // elements per field plane: nz * ny * pitch
+    long long vstride;     // elements per version slot: m * fstride
+    long long offset;      // element offset of slot 0, field 0 in the state pool
+    long long aux_offset;  // element offset of the (Z, c) planes in the aux pool, or -1
+    double dx[3];
+    int bc[6];
+    int ndim;
+    int pad;
+};
+
+// Per-instance step control, resident on the device; only the step-control
+// kernels write it (the sweeps read t, dt_attempt, cur[] and active, and
+// accumulate smax / bad with atomics).
+struct Control {
+    double t;              // simulated time of the kept state
+    double dt;             // proposal for the next step (cfl_desired / M)
+    double t_final;        // target of kModeTFinal
+    double dt_attempt;     // step size the sweeps of the current attempt use
+    double fixed_dt;       // > 0: fixed step, no CFL control
+    double cfl_last;       // Courant number of the last attempt
+    double cfl_desired;
+    double cfl_max;
+    double dt_max;
+    double M_last;         // max_d(m_d / dx_d) of the last attempt or speed pass
+    long long nacc;        // accepted steps
+    long long nrej;        // rejected attempts
+    long long target;      // kModeSteps: accept until nacc == target
+    unsigned long long smax[3];  // bits of max|s| (as double) per direction
+    int cur[4];            // version slot holding each field's kept state
+    int mode;
+    int active;            // the current attempt runs
+    int last;              // the current attempt lands on t_final
+    int streak;            // consecutive rejections
+    int max_retries;
+    unsigned status;       // latched kStat* bits
+    unsigned bad;          // non-physical state seen in the current attempt
+    int pad;
+};
+
+// One tile of a sweep: kLines consecutive lines of one instance and the
+// segment [a, b) of each line along the sweep direction.  For the x sweep the
+// lines are rows r = line0 + t of the flattened (z, y) index; for the y (z)
+// sweep they are columns x = line0 + t of plane z = other (row y = other).
+struct TileDesc {
+    int inst;
+    int line0;
+    int other;
+    int a, b;
+    int pad[3];
+};
+
+// Per-sweep description of which version slot each field is read from and
+// written to, relative to the field's kept slot (Control::cur).
+struct SlotMap {
+    signed char in_off[4];
+    signed char out_off[4];
+};
+
+struct SweepArgs {
+    const TileDesc* tiles;
+    const InstDesc* inst;
+    Control* ctl;
+    void* pool;            // state pool (float or double elements)
+    const void* aux;       // aux pool: (Z, c) planes per instance
+    int ntiles;
+    int inst_lo, inst_hi;  // instances this launch may touch
+    SlotMap slots;
+    double Z, c, g;        // constant acoustics impedance / speed; gravity
+};
+
+}  // namespace claw

@@ -1,0 +1,239 @@
+// Point-wise Riemann solvers as device functors (CUDACLAW Sec. 4.2: a
+// solver is a scalar function of the two cell states beside one interface;
+// the framework maps threads onto interfaces around it).  A new PDE system
+// plugs in by providing one such struct:
+//
+//   NQ      components of the reduced state a sweep touches; component 0 is
+//           the scalar (p or h), 1 the velocity / momentum normal to the
+//           sweep, 2.. transverse components that waves carry
+//   NW      waves per interface;  NA  material values per cell
+//   Cell    per-cell registers: q[NQ] plus whatever the solver precomputes
+//           once per cell (it is shared by the cell's two interfaces)
+//   field(d, c)        state field that reduced component c maps to
+//   prepare(cell, P)   fill the precomputed part of a freshly loaded cell
+//   solve(l, r, P, w)  waves w.W[p][c], speeds w.s[p], fluctuations
+//                      w.amdq[c] (A-dQ), w.apdq[c] (A+dQ)
+//   nonphysical(q)     true for a state the method cannot continue from
+//
+// Formulas the paper leaves to its textbook reference are the standard ones:
+// linear acoustics with per-cell impedance, and Roe's linearisation for
+// shallow water with the Harten-Hyman entropy fix.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace claw {
+
+template <class Real, int NQ, int NW>
+struct Waves {
+    Real W[NW][NQ];
+    Real s[NW];
+    Real amdq[NQ];
+    Real apdq[NQ];
+};
+
+template <class Real>
+__device__ __forceinline__ bool finite_(Real x) {
+    return fabs(x) <= (Real)INFINITY && x == x;
+}
+
+// ------------------------------------------------------------------------
+// Linear acoustics, Sec. 3 Eq. acoustics with coefficients:
+//   p_t + K div u = 0,  rho u_t + grad p = 0.
+// Along a direction the normal system has speeds -c, +c (c = sqrt(K/rho))
+// and eigenvectors (-Z, 1), (Z, 1) with impedance Z = rho c.  With
+// different cells on the two sides the left-going wave takes the left
+// cell's (Z, c) and the right-going wave the right cell's:
+//   alpha1 = (-dp + Z_r du) / (Z_l + Z_r),  alpha2 = (dp + Z_l du) / (Z_l + Z_r).
+// VAR = false: one (Z, c) for the whole grid (kernel parameters).
+// ------------------------------------------------------------------------
+template <class Real, bool VAR>
+struct Acoustics {
+    static constexpr int NQ = 2;
+    static constexpr int NW = 2;
+    static constexpr int NA = VAR ? 2 : 0;
+    struct Params {
+        Real Z, c, inv2Z;
+    };
+    struct Cell {
+        Real q[NQ];
+        Real Z, c;
+    };
+
+    __device__ __forceinline__ static int field(int d, int comp) { return comp == 0 ? 0 : 1 + d; }
+
+    __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
+        if (!VAR) {
+            cell.Z = P.Z;
+            cell.c = P.c;
+        }
+    }
+
+    __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
+                                                 Waves<Real, NQ, NW>& w) {
+        const Real dp = r.q[0] - l.q[0];
+        const Real du = r.q[1] - l.q[1];
+        const Real inv = VAR ? Real(1) / (l.Z + r.Z) : P.inv2Z;
+        const Real a1 = (r.Z * du - dp) * inv;
+        const Real a2 = (dp + l.Z * du) * inv;
+        w.W[0][0] = -a1 * l.Z;
+        w.W[0][1] = a1;
+        w.s[0] = -l.c;
+        w.W[1][0] = a2 * r.Z;
+        w.W[1][1] = a2;
+        w.s[1] = r.c;
+        // c > 0: the first wave always goes left, the second right.
+        w.amdq[0] = w.s[0] * w.W[0][0];
+        w.amdq[1] = w.s[0] * w.W[0][1];
+        w.apdq[0] = w.s[1] * w.W[1][0];
+        w.apdq[1] = w.s[1] * w.W[1][1];
+    }
+
+    // Interface speeds only (CFL pass).
+    __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params&,
+                                                  Real s[NW]) {
+        s[0] = -l.c;
+        s[1] = r.c;
+    }
+
+    __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
+        return !(finite_(q[0]) && finite_(q[1]));
+    }
+};
+
+// ------------------------------------------------------------------------
+// Shallow water, Sec. 3 Eq. SW, reduced state (h, h u_n, h u_t).
+// Roe averages h_bar = (h_l + h_r)/2, u_hat, v_hat weighted by sqrt(h),
+// c_hat = sqrt(g h_bar); speeds u_hat -/+ c_hat and u_hat; eigenvectors
+// r1 = (1, u_hat - c_hat, v_hat), r2 = (0, 0, 1), r3 = (1, u_hat + c_hat, v_hat).
+// Harten-Hyman: a 1-wave with u_l - c_l < 0 < u_m - c_m at the middle
+// state q_m = Q_l + W1 (a transonic rarefaction) is split with
+// beta = (lam_m - s1) / (lam_m - lam_l) into beta lam_l W1 (left) and
+// (1 - beta) lam_m W1 (right); the 3-wave mirrors this with
+// q_m = Q_r - W3.  The sign test of lam_m is done without a square root:
+// for h_m > 0, u_m - sqrt(g h_m) > 0  <=>  hu_m > 0 and hu_m^2 > g h_m^3.
+// ------------------------------------------------------------------------
+template <class Real>
+struct ShallowWater {
+    static constexpr int NQ = 3;
+    static constexpr int NW = 3;
+    static constexpr int NA = 0;
+    struct Params {
+        Real g, half_g;
+    };
+    struct Cell {
+        Real q[NQ];
+        Real u, v;   // velocities
+        Real sqh;    // sqrt(h)
+        Real c;      // sqrt(g h)
+    };
+
+    __device__ __forceinline__ static int field(int d, int comp) {
+        return comp == 0 ? 0 : (comp == 1 ? 1 + d : 2 - d);
+    }
+
+    __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
+        const Real rh = Real(1) / cell.q[0];
+        cell.u = cell.q[1] * rh;
+        cell.v = cell.q[2] * rh;
+        cell.sqh = sqrt(cell.q[0]);
+        cell.c = sqrt(P.g * cell.q[0]);
+    }
+
+    __device__ __forceinline__ static void roe(const Cell& l, const Cell& r, const Params& P,
+                                               Real& uh, Real& vh, Real& ch) {
+        const Real den = Real(1) / (l.sqh + r.sqh);
+        uh = (l.sqh * l.u + r.sqh * r.u) * den;
+        vh = (l.sqh * l.v + r.sqh * r.v) * den;
+        ch = sqrt(P.g * (Real(0.5) * (l.q[0] + r.q[0])));
+    }
+
+    __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
+                                                 Waves<Real, NQ, NW>& w) {
+        Real uh, vh, ch;
+        roe(l, r, P, uh, vh, ch);
+        const Real d0 = r.q[0] - l.q[0];
+        const Real d1 = r.q[1] - l.q[1];
+        const Real d2 = r.q[2] - l.q[2];
+        const Real i2c = Real(0.5) / ch;
+        const Real s1 = uh - ch, s3 = uh + ch;
+        const Real a1 = (s3 * d0 - d1) * i2c;
+        const Real a2 = d2 - vh * d0;
+        const Real a3 = (d1 - s1 * d0) * i2c;
+        w.s[0] = s1;
+        w.s[1] = uh;
+        w.s[2] = s3;
+        w.W[0][0] = a1;
+        w.W[0][1] = a1 * s1;
+        w.W[0][2] = a1 * vh;
+        w.W[1][0] = Real(0);
+        w.W[1][1] = Real(0);
+        w.W[1][2] = a2;
+        w.W[2][0] = a3;
+        w.W[2][1] = a3 * s3;
+        w.W[2][2] = a3 * vh;
+
+        // Split factors: A-dQ = sum km_p W_p, A+dQ = sum kp_p W_p.
+        Real km1 = fmin(s1, Real(0)), kp1 = fmax(s1, Real(0));
+        Real km3 = fmin(s3, Real(0)), kp3 = fmax(s3, Real(0));
+        const Real km2 = fmin(uh, Real(0)), kp2 = fmax(uh, Real(0));
+
+        const Real lam_l = l.u - l.c;
+        if (lam_l < Real(0)) {
+            const Real hm = l.q[0] + w.W[0][0];
+            const Real hum = l.q[1] + w.W[0][1];
+            if (hm > Real(0) && hum > Real(0) && hum * hum > P.g * hm * hm * hm) {
+                const Real lam_m = hum / hm - sqrt(P.g * hm);
+                const Real beta = (lam_m - s1) / (lam_m - lam_l);
+                km1 = beta * lam_l;
+                kp1 = (Real(1) - beta) * lam_m;
+            }
+        }
+        const Real lam_r = r.u + r.c;
+        if (lam_r > Real(0)) {
+            const Real hm = r.q[0] - w.W[2][0];
+            const Real hum = r.q[1] - w.W[2][1];
+            if (hm > Real(0) && hum < Real(0) && hum * hum > P.g * hm * hm * hm) {
+                const Real lam_m = hum / hm + sqrt(P.g * hm);
+                const Real beta = (lam_r - s3) / (lam_r - lam_m);
+                km3 = beta * lam_m;
+                kp3 = (Real(1) - beta) * lam_r;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            w.amdq[c] = km1 * w.W[0][c] + km2 * w.W[1][c] + km3 * w.W[2][c];
+            w.apdq[c] = kp1 * w.W[0][c] + kp2 * w.W[1][c] + kp3 * w.W[2][c];
+        }
+    }
+
+    __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params& P,
+                                                  Real s[NW]) {
+        Real uh, vh, ch;
+        roe(l, r, P, uh, vh, ch);
+        s[0] = uh - ch;
+        s[1] = uh;
+        s[2] = uh + ch;
+    }
+
+    __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
+        return !(q[0] > Real(0) && finite_(q[0]) && finite_(q[1]) && finite_(q[2]));
+    }
+};
+
+// ------------------------------------------------------------------------
+// Wave limiters phi(theta) (Sec. 3, the wave limiter), theta the ratio of
+// the upwind wave's projection to the wave's own norm.  fmin/fmax return the
+// non-NaN operand, so a zero wave (theta = 0/0) still limits to zero.
+// ------------------------------------------------------------------------
+enum : int { kLimNone = 0, kLimMinmod = 1, kLimMC = 2 };
+
+template <int LIM, class Real>
+__device__ __forceinline__ Real limiter_phi(Real theta) {
+    if (LIM == kLimMinmod) return fmax(Real(0), fmin(Real(1), theta));
+    if (LIM == kLimMC)
+        return fmax(Real(0), fmin(fmin(Real(0.5) * (Real(1) + theta), Real(2)), Real(2) * theta));
+    return Real(1);
+}
+
+}  // namespace claw

@@ -1,0 +1,37 @@
+// Compile-time dispatch of the sweep kernel over limiter, direction and
+// pass kind; each instantiation unit includes this for one (system, Real).
+#pragma once
+#include "launch.h"
+#include "sweep.cuh"
+
+namespace claw {
+
+template <class Sys, class Real, int LIM, int DIR, bool SPEEDS>
+cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
+    if (L.grid == 0) return cudaSuccess;
+    sweep_kernel<Sys, Real, LIM, DIR, SPEEDS><<<L.grid, kLines, 0, L.stream>>>(L.args, P);
+    return cudaGetLastError();
+}
+
+template <class Sys, class Real, int DIR>
+cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P) {
+    if (L.speeds) return sweep_go<Sys, Real, kLimNone, DIR, true>(L, P);
+    switch (L.limiter) {
+        case kLimNone: return sweep_go<Sys, Real, kLimNone, DIR, false>(L, P);
+        case kLimMinmod: return sweep_go<Sys, Real, kLimMinmod, DIR, false>(L, P);
+        default: return sweep_go<Sys, Real, kLimMC, DIR, false>(L, P);
+    }
+}
+
+template <class Sys, class Real, bool HAS_Z>
+cudaError_t sweep_by_dir(const SweepLaunch& L, const typename Sys::Params& P) {
+    switch (L.dir) {
+        case 0: return sweep_by_limiter<Sys, Real, 0>(L, P);
+        case 1: return sweep_by_limiter<Sys, Real, 1>(L, P);
+        default:
+            if constexpr (HAS_Z) return sweep_by_limiter<Sys, Real, 2>(L, P);
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace claw

@@ -1,0 +1,286 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the FP64 path must match the oracle to 1e-12 relative L-inf per
+field after the stated number of steps; the FP32 form to 1e-5 relative L2
+(acoustics) and 1e-4 relative L1 on h (shallow water).  The time-step
+sequence (t, dt, accepted steps) must agree as well.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle
+from paper_1805_08846_gb300 import ClawError, Ensemble, Solver, inputs
+from paper_1805_08846_gb300 import _lib as L
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def fieldwise_linf(a, b):
+    return max(oracle.rel_linf(a[f], b[f]) for f in range(a.shape[0]))
+
+
+def check_fp32(prob, q32, qref):
+    if prob.system == "shallow_water":
+        err = oracle.rel_l1(q32[0], qref[0])
+        assert err <= 1e-4, err
+    else:
+        err = max(oracle.rel_l2(q32[f], qref[f]) for f in range(q32.shape[0])
+                  if np.abs(qref[f]).max() > 0)
+        assert err <= 1e-5, err
+    return err
+
+
+def run_both(prob, nsteps, precision=64, seg=None):
+    ref = Oracle(prob).run_steps(prob.q0, nsteps)
+    with Solver.from_problem(prob, precision=precision) as s:
+        if seg is not None:
+            for d in range(prob.ndim):
+                s.set_segment(d, seg)
+        s.run_steps(nsteps)
+        q = s.get_q()
+        t, dt, n = s.time()
+    return q, (t, dt, n), ref
+
+
+def test_config1_acoustics_128_full_100_steps():
+    """2D acoustics, 128^2, MC, walls, CFL 0.9, 100 steps, FP64."""
+    prob = inputs.acoustics_2d_pulse(128)
+    q, (t, dt, n), ref = run_both(prob, 100)
+    assert n == 100 and ref["nacc"] == 100
+    assert dt == ref["dt"] == 0.9 / 256
+    assert t == pytest.approx(ref["t"], rel=1e-15)
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+CASES = []
+for system in ("acoustics", "shallow_water"):
+    for limiter in ("none", "minmod", "mc"):
+        for bc in ("periodic", "extrap", "wall"):
+            CASES.append((system, (37, 29), limiter, bc))
+CASES += [("acoustics", (130, 67), "mc", ("wall", "extrap", "periodic", "wall")),
+          ("shallow_water", (131, 257), "minmod", ("extrap", "wall", "periodic", "periodic")),
+          ("acoustics_var", (23, 19, 21), "mc", "wall"),
+          ("acoustics_var", (40, 9, 7), "minmod", ("periodic", "periodic", "extrap", "wall", "wall", "extrap")),
+          ("acoustics", (17, 21, 25), "none", "periodic"),
+          ("acoustics_var", (150, 20), "mc", "periodic")]
+
+
+@pytest.mark.parametrize("system,shape,limiter,bc", CASES)
+@pytest.mark.parametrize("precision", [64, 32])
+def test_small_grids_every_system_limiter_bc(system, shape, limiter, bc, precision):
+    prob = inputs.random_problem(system, shape, limiter, bc, discontinuous=True)
+    q, (t, dt, n), ref = run_both(prob, 12, precision)
+    assert n == 12
+    if precision == 64:
+        assert fieldwise_linf(q, ref["q"]) <= TOL64
+        assert t == pytest.approx(ref["t"], rel=1e-13)
+    else:
+        check_fp32(prob, q, ref["q"])
+        assert t == pytest.approx(ref["t"], rel=1e-5)
+
+
+@pytest.mark.parametrize("seg", [4, 5, 17, 1000])
+def test_segment_lengths_do_not_change_the_result(seg):
+    """Lines split into segments of any length give the oracle's result."""
+    prob = inputs.random_problem("shallow_water", (61, 45), "mc", ("periodic", "wall", "extrap", "wall"),
+                                 discontinuous=True)
+    q, _, ref = run_both(prob, 6, 64, seg=seg)
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+def test_initial_dt_from_speed_pass():
+    prob = inputs.sw_radial_dam_break(96)
+    M = Oracle(prob).max_speed_over_dx(prob.q0)
+    with Solver.from_problem(prob, 64) as s:
+        t, dt, n = s.time()
+        assert (t, n) == (0.0, 0)
+        assert dt == pytest.approx(0.9 / M, rel=1e-14)
+        assert s.max_speed() == pytest.approx(M, rel=1e-14)
+
+
+def test_advance_matches_oracle_and_lands_on_t_final():
+    prob = inputs.sw_radial_dam_break(80)
+    ref = Oracle(prob).advance(prob.q0, 0.05)
+    with Solver.from_problem(prob, 64) as s:
+        nst = s.advance(0.05)
+        q = s.get_q()
+        t, dt, n = s.time()
+    assert t == 0.05 and nst == ref["nacc"]
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+def test_cfl_rejection_is_redone_like_the_oracle():
+    prob = inputs.acoustics_2d_pulse(40)
+    dt_bad = 1.5 / (2.0 * 40)
+    ref = Oracle(prob).run_steps(prob.q0, 3, dt=dt_bad)
+    assert ref["nrej"] == 1
+    with Solver.from_problem(prob, 64) as s:
+        s.set_time(0.0, dt_bad, 0)
+        s.run_steps(3)
+        q = s.get_q()
+        t, dt, n = s.time()
+        assert s.rejections() == 1
+    assert n == 3 and t == pytest.approx(ref["t"], rel=1e-15)
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+def test_fixed_dt_step():
+    prob = inputs.random_problem("acoustics", (33, 31), "mc", "periodic")
+    dt = 0.3 * prob.dx[0] / 2.0
+    ref = Oracle(prob).run_steps(prob.q0, 4, fixed_dt=dt)
+    with Solver.from_problem(prob, 64) as s:
+        for _ in range(4):
+            s.step(dt)
+        q = s.get_q()
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("bc", ["periodic", "extrap", "wall"])
+def test_lake_at_rest_bitwise(precision, bc):
+    q0 = np.zeros((3, 45, 77))
+    q0[0] = 1.3
+    prob = inputs.Problem(2, (77, 45), (0, 0), (1, 1), "shallow_water", "mc", (bc,) * 4, q0)
+    with Solver.from_problem(prob, precision) as s:
+        s.run_steps(25)
+        q = s.get_q()
+    np.testing.assert_array_equal(q, q0)
+
+
+def test_conservation_sums_on_device():
+    prob = inputs.random_problem("shallow_water", (64, 48), "minmod", "periodic", discontinuous=True)
+    with Solver.from_problem(prob, 64) as s:
+        s0 = s.sums()
+        s.run_steps(30)
+        s1 = s.sums()
+        q = s.get_q()
+    np.testing.assert_allclose(s0, [math.fsum(prob.q0[f].ravel()) for f in range(3)], rtol=1e-14)
+    np.testing.assert_allclose(s1, [math.fsum(q[f].ravel()) for f in range(3)], rtol=1e-14)
+    assert abs(s1[0] - s0[0]) <= 1e-13 * abs(s0[0])
+
+
+def test_checkpoint_resume_is_bitwise():
+    prob = inputs.random_problem("shallow_water", (50, 40), "mc", "wall", discontinuous=True)
+    with Solver.from_problem(prob, 64) as s:
+        s.run_steps(20)
+        q_all = s.get_q()
+        t_all = s.time()
+    with Solver.from_problem(prob, 64) as s:
+        s.run_steps(8)
+        q8 = s.get_q()
+        t8 = s.time()
+    with Solver.from_problem(prob, 64) as s:
+        s.set_q(q8)
+        s.set_time(*t8)
+        s.run_steps(12)
+        q_res = s.get_q()
+        t_res = s.time()
+    np.testing.assert_array_equal(q_res, q_all)
+    assert t_res == t_all
+
+
+def test_device_tensors_through_the_abi():
+    torch = pytest.importorskip("torch")
+    prob = inputs.random_problem("acoustics", (40, 30), "mc", "wall")
+    ref = Oracle(prob).run_steps(prob.q0, 5)
+    with Solver.from_problem(prob, 64, stream="torch") as s:
+        q_dev = torch.from_numpy(prob.q0).cuda()
+        torch.cuda.synchronize()
+        s.set_q(q_dev)
+        s.run_steps(5)
+        out = torch.empty(prob.q0.shape, dtype=torch.float64, device="cuda")
+        s.get_q(out)
+        torch.cuda.synchronize()
+    assert fieldwise_linf(out.cpu().numpy(), ref["q"]) <= TOL64
+
+
+# ------------------------------------------------------------------ faults
+
+def test_nan_state_is_reported():
+    prob = inputs.random_problem("acoustics", (20, 20), "mc", "wall")
+    q = prob.q0.copy()
+    q[0, 5, 5] = np.nan
+    with Solver.from_problem(prob.with_(q0=q), 64) as s:
+        with pytest.raises(ClawError) as ei:
+            s.run_steps(2)
+        assert ei.value.status == L.CLAW_ENONPHYS
+
+
+def test_negative_depth_is_reported():
+    prob = inputs.random_problem("shallow_water", (20, 20), "minmod", "wall")
+    q = prob.q0.copy()
+    q[0, 3, 4] = -0.5
+    with pytest.raises(ClawError) as ei:
+        with Solver.from_problem(prob.with_(q0=q), 64) as s:
+            s.run_steps(2)
+    assert ei.value.status == L.CLAW_ENONPHYS
+
+
+def test_repeated_cfl_rejection_is_reported():
+    """cfl_desired above cfl_max can never be kept: after max_retries
+    consecutive rejections the run stops with CLAW_ECFL."""
+    prob = inputs.acoustics_2d_pulse(24).with_(cfl_desired=1.5)
+    with Solver.from_problem(prob, 64, max_retries=3) as s:
+        with pytest.raises(ClawError) as ei:
+            s.run_steps(1)
+        assert ei.value.status == L.CLAW_ECFL
+
+
+def test_t_final_in_the_past_is_rejected():
+    prob = inputs.acoustics_2d_pulse(16)
+    with Solver.from_problem(prob, 64) as s:
+        s.run_steps(2)
+        with pytest.raises(ClawError) as ei:
+            s.advance(0.0)
+        assert ei.value.status == L.CLAW_EINVAL
+
+
+# ------------------------------------------------------------------ ensembles
+
+def test_small_sw_ensemble_matches_oracle_per_instance():
+    probs = inputs.sw_ensemble(B=6, nmin=16, nmax=90, nsteps=10)
+    for prec in (64, 32):
+        e = Ensemble.from_problems(probs, precision=prec)
+        e.run_steps(10)
+        for i, p in enumerate(probs):
+            ref = Oracle(p).run_steps(p.q0, 10)
+            q = e.get_q(i)
+            t, dt, n = e.time(i)
+            assert n == 10
+            if prec == 64:
+                assert fieldwise_linf(q, ref["q"]) <= TOL64
+                assert t == pytest.approx(ref["t"], rel=1e-14)
+            else:
+                check_fp32(p, q, ref["q"])
+        e.close()
+
+
+def test_small_acoustics3d_ensemble_matches_oracle_per_instance():
+    probs = inputs.acoustics3d_ensemble(B=4, nmin=9, nmax=24, nsteps=8)
+    for prec in (64, 32):
+        e = Ensemble.from_problems(probs, precision=prec)
+        e.run_steps(8)
+        for i, p in enumerate(probs):
+            ref = Oracle(p).run_steps(p.q0, 8)
+            q = e.get_q(i)
+            if prec == 64:
+                assert fieldwise_linf(q, ref["q"]) <= TOL64
+            else:
+                check_fp32(p, q, ref["q"])
+        e.close()
+
+
+def test_ensemble_instances_keep_their_own_time_steps():
+    probs = inputs.sw_ensemble(B=3, nmin=20, nmax=60)
+    e = Ensemble.from_problems(probs, precision=64)
+    e.run_steps(5)
+    dts = [e.time(i)[1] for i in range(3)]
+    refs = [Oracle(p).run_steps(p.q0, 5)["dt"] for p in probs]
+    np.testing.assert_allclose(dts, refs, rtol=1e-14)
+    assert len(set(dts)) == 3
+    e.close()
