@@ -149,7 +149,8 @@ def test_lake_at_rest_bitwise(precision, bc):
     with Solver.from_problem(prob, precision) as s:
         s.run_steps(25)
         q = s.get_q()
-    np.testing.assert_array_equal(q, q0)
+    kept = q0 if precision == 64 else q0.astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(q, kept)
 
 
 def test_conservation_sums_on_device():
