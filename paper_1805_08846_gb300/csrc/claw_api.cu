@@ -636,11 +636,13 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
     for (int k = 0; k < nsteps && st == CLAW_OK; ++k) {
         for (int d = 0; d <= s->ndim && st == CLAW_OK; ++d) {
             cudaEvent_t* e = &ev[((size_t)k * nk + d) * 2];
-            cudaEventRecord(e[0], s->stream);
+            // External records become event nodes of the graph (timestamps),
+            // not just capture dependencies.
+            cudaEventRecordWithFlags(e[0], s->stream, cudaEventRecordExternal);
             if (d < s->ndim) st = launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false);
             else if (launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->stream) != cudaSuccess)
                 st = fail(CLAW_ECUDA, "finish launch failed");
-            cudaEventRecord(e[1], s->stream);
+            cudaEventRecordWithFlags(e[1], s->stream, cudaEventRecordExternal);
         }
     }
     cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
