@@ -169,6 +169,42 @@ claw_status claw_ensemble_run_steps(claw_solver* s, int nsteps);
 claw_status claw_ensemble_get_time(claw_solver* s, int i, double* t, double* dt, long* nsteps);
 int         claw_ensemble_size(const claw_solver* s);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* The CFL speed pass of claw_max_speed over a caller-owned state, without
+ * creating a solver and without allocating anything.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * (cudaMalloc, cudaFree or any allocating library routine) -- for example a
+ * host framework that owns every byte of device memory through its own
+ * pool, or a latency-critical loop where an allocation could synchronise
+ * the device -- but already hold the state on the GPU.
+ *
+ *   q        FP64 device array, SoA q[f][z][y][x], interior cells, m fields
+ *            (m = 3 for 2D acoustics and shallow water, 4 for 3D acoustics)
+ *   rho, K   FP64 device arrays of nx*ny*nz cells for CLAW_ACOUSTICS_VAR,
+ *            else ignored (may be NULL); params->rho, K, g give the constants
+ *   out      device pointer to one double: max_d (max|s^p| / dx_d), computed
+ *            in FP64 like claw_max_speed of a precision-64 solver; NaN if a
+ *            speed is not finite
+ *   cuda_stream  stream both kernels run on (NULL = legacy default stream)
+ *
+ * Scratch: a fixed 384 KiB array in the library's device memory (one
+ * partial maximum per 128 lines per direction) that every GPU loading the
+ * library holds until the process exits.  Grids with more than 2,097,152
+ * lines in some direction are rejected with CLAW_EBOUNDS.  All calls share
+ * the array and it keeps the last call's contents; calls that overlap on the
+ * GPU (different streams, or devices sharing nothing else) race on it, so
+ * serialise them.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Asynchronous on cuda_stream: *out
+ * is valid once the stream reaches it.  Errors: CLAW_EINVAL for bad
+ * arguments, CLAW_EBOUNDS for oversized grids, CLAW_ECUDA if the lookup or a
+ * launch fails (message in claw_last_error()). */
+claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system system,
+                                   const claw_bc bc[6], const claw_params* params,
+                                   const double* q, const double* rho, const double* K,
+                                   double* out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Take nsteps accepted steps like claw_run_steps inside one CUDA graph whose

@@ -68,6 +68,8 @@ _SIGS = {
     "claw_ensemble_size": [_vp],
     "claw_profile_steps": [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_long)],
     "claw_set_segment": [_vp, C.c_int, C.c_int],
+    "claw_max_speed_noalloc": [C.POINTER(claw_grid), C.c_int, C.POINTER(C.c_int),
+                               C.POINTER(claw_params), _vp, _vp, _vp, _vp, _vp],
 }
 
 _lib = None
@@ -287,3 +289,16 @@ def claw_profile_steps(h, nsteps):
 
 def claw_set_segment(h, d, seg_len):
     _check(lib().claw_set_segment(h, int(d), int(seg_len)), "claw_set_segment")
+
+
+def claw_max_speed_noalloc(n, dx, system, bc, params, q_dev, out_dev, rho_dev=None, K_dev=None,
+                           stream=None):
+    """CFL speed pass over caller-owned device tensors, allocating nothing:
+    ``q_dev`` (float64 CUDA tensor, SoA), ``out_dev`` (one float64 on the
+    device) receives max_d(max|s| / dx_d) asynchronously on ``stream``."""
+    g = make_grid(n, dx)
+    sysc = SYSTEMS[system] if isinstance(system, str) else int(system)
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    _check(lib().claw_max_speed_noalloc(C.byref(g), sysc, make_bc(bc, len(n)), C.byref(params),
+                                        ptr(q_dev), ptr(rho_dev), ptr(K_dev), ptr(out_dev),
+                                        _stream_arg(stream)), "claw_max_speed_noalloc")

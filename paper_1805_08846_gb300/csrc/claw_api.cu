@@ -452,6 +452,8 @@ claw_status set_aux_impl(claw_solver* s, int i, const double* rho, const double*
 
 }  // namespace
 
+void claw::set_last_error(const char* msg) { g_err = msg; }
+
 cudaError_t claw::launch_sweep(const SweepLaunch& L) {
     switch (L.system) {
         case kSysAcoustics:

@@ -18,6 +18,9 @@ struct SweepLaunch {
     cudaStream_t stream;
 };
 
+// Record the thread-local message claw_last_error() returns.
+void set_last_error(const char* msg);
+
 // Dispatch to the (system, precision) instantiation unit.
 cudaError_t launch_sweep(const SweepLaunch& L);
 cudaError_t launch_sweep_acoustics_f32(const SweepLaunch& L);
