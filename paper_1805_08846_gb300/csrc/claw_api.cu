@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/claw.h: argument checks, device
 // memory, tile lists, CUDA graphs of step attempts, and status reporting.
 #include <claw.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -61,6 +62,7 @@ struct claw_solver {
     int bc[6]{};
     std::vector<InstDesc> inst;
     InstDesc* d_inst = nullptr;
+    TmaSet* d_tma = nullptr;
     Control* d_ctl = nullptr;
     Control* h_ctl = nullptr;  // pinned mirror for reads
     void* pool = nullptr;
@@ -140,6 +142,8 @@ SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi) {
     a.tiles = s->d_tiles[d] + tile_lo;
     a.ntiles = tile_hi - tile_lo;
     a.inst = s->d_inst;
+    a.tma = s->d_tma;
+    a.m = s->m;
     a.ctl = s->d_ctl;
     a.pool = s->pool;
     a.aux = s->aux;
@@ -261,6 +265,66 @@ claw_status run_armed(claw_solver* s, int mode, long long nsteps) {
     return latched_status(s, 0, s->B);
 }
 
+// ---------------------------------------------------------------- TMA descriptors
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+claw_status encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
+                   const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swz) {
+    auto fn = encode_fn();
+    if (!fn) return fail(CLAW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(map, dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CLAW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return CLAW_OK;
+}
+
+// State planes (3 slots x m fields) and material planes of instance i viewed
+// for the x sweep (rows of the flattened (z, y) index) and the y / z sweeps.
+claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
+    memset(&T, 0, sizeof T);
+    const InstDesc& I = s->inst[i];
+    const CUtensorMapDataType dt = s->precision == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t es = s->esize;
+    const cuuint32_t cx = (cuuint32_t)(32 / es);   // 32-byte rows for the x sweep
+    const cuuint32_t ct = (cuuint32_t)(32 / es);   // cells per chunk along y / z (4 KB boxes)
+    for (int kind = 0; kind < 2; ++kind) {
+        if (kind == 1 && s->system != CLAW_ACOUSTICS_VAR) break;
+        char* base = kind == 0 ? (char*)s->pool + I.offset * es : (char*)s->aux + I.aux_offset * es;
+        const cuuint64_t planes = kind == 0 ? 3 * (cuuint64_t)s->m : 2;
+        {
+            const cuuint64_t dims[3] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1] * I.n[2], planes};
+            const cuuint64_t str[2] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.fstride * es};
+            const cuuint32_t box[3] = {cx, (cuuint32_t)kLines, 1};
+            CKS(encode(&T.map[3 * kind + 0], dt, 3, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B));
+        }
+        const cuuint64_t dims[4] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1], (cuuint64_t)I.n[2], planes};
+        const cuuint64_t str[3] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.n[1] * I.pitch * es,
+                                   (cuuint64_t)I.fstride * es};
+        {
+            const cuuint32_t box[4] = {(cuuint32_t)kLines, ct, 1, 1};
+            CKS(encode(&T.map[3 * kind + 1], dt, 4, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE));
+        }
+        if (s->ndim == 3) {
+            const cuuint32_t box[4] = {(cuuint32_t)kLines, 1, ct, 1};
+            CKS(encode(&T.map[3 * kind + 2], dt, 4, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE));
+        }
+    }
+    return CLAW_OK;
+}
+
 claw_status speed_pass(claw_solver* s, int i, int set_dt) {
     for (int d = 0; d < s->ndim; ++d) {
         auto r = s->inst_tiles[d][i];
@@ -354,6 +418,12 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
     CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
     CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
+    {
+        std::vector<TmaSet> tma(B);
+        for (int i = 0; i < B; ++i) CKS(encode_instance(s, i, tma[i]));
+        CK(cudaMalloc(&s->d_tma, sizeof(TmaSet) * B));
+        CK(cudaMemcpy(s->d_tma, tma.data(), sizeof(TmaSet) * B, cudaMemcpyHostToDevice));
+    }
 
     std::vector<Control> ctl(B);
     for (int i = 0; i < B; ++i) {
@@ -511,6 +581,7 @@ void claw_destroy(claw_solver* s) {
     if (s->stage) cudaFree(s->stage);
     if (s->d_sums) cudaFree(s->d_sums);
     if (s->d_inst) cudaFree(s->d_inst);
+    if (s->d_tma) cudaFree(s->d_tma);
     if (s->d_ctl) cudaFree(s->d_ctl);
     if (s->h_ctl) cudaFreeHost(s->h_ctl);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -617,7 +688,8 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
     if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
     if (seg_len < 4) return fail(CLAW_EINVAL, "segment length must be >= 4");
     CK(cudaStreamSynchronize(s->stream));
-    s->seg[d] = seg_len;
+    // x segments start on 32-byte boundaries (the bulk copies' alignment rule)
+    s->seg[d] = d == 0 ? (seg_len + 7) / 8 * 8 : seg_len;
     return build_tiles(s);
 }
 

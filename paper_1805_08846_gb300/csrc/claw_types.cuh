@@ -1,6 +1,7 @@
 // Device/host data structures shared by the sweep kernels, the step-control
 // kernels and the host API of the wave-propagation library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,8 +85,15 @@ struct SlotMap {
     signed char out_off[4];
 };
 
+// Bulk-tensor (TMA) descriptors of one instance: state planes viewed for the
+// x, y and z sweeps, and the same three views of the (Z, c) material planes.
+struct alignas(64) TmaSet {
+    CUtensorMap map[6];
+};
+
 struct SweepArgs {
     const TileDesc* tiles;
+    const TmaSet* tma;
     const InstDesc* inst;
     Control* ctl;
     void* pool;            // state pool (float or double elements)
@@ -93,6 +101,7 @@ struct SweepArgs {
     int ntiles;
     int inst_lo, inst_hi;  // instances this launch may touch
     SlotMap slots;
+    int m;                 // fields per state version (TMA plane = slot * m + field)
     double Z, c, g;        // constant acoustics impedance / speed; gravity
 };
 

@@ -69,6 +69,10 @@ __global__ void finish_kernel(Control* ctl, const InstDesc* inst, int lo, int hi
     Control& c = ctl[i];
     if (!c.active) return;
     const InstDesc& I = inst[i];
+    if (c.status) {   // a sweep latched a fault (e.g. a timed-out copy): keep nothing
+        c.active = 0;
+        return;
+    }
     double M = 0.0;
     bool nonfinite = false;
     for (int d = 0; d < I.ndim; ++d) {

@@ -37,6 +37,26 @@ __device__ __forceinline__ bool finite_(Real x) {
     return fabs(x) <= (Real)INFINITY && x == x;
 }
 
+// Division, reciprocal and square roots.  FP64 (the plain path) uses the
+// correctly rounded operations; the FP32 form uses the SFU approximations
+// (reciprocal and reciprocal square root, a few ulp), far inside its
+// 1e-4 / 1e-5 error budget and a fraction of the instruction count.
+template <class Real>
+struct Ops;
+template <>
+struct Ops<double> {
+    __device__ __forceinline__ static double div(double a, double b) { return a / b; }
+    __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }
+    __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
+};
+template <>
+struct Ops<float> {
+    __device__ __forceinline__ static float div(float a, float b) { return __fdividef(a, b); }
+    __device__ __forceinline__ static float rcp(float x) { return __fdividef(1.0f, x); }
+    // x > 0: x * rsqrt(x)
+    __device__ __forceinline__ static float sqrt_(float x) { return x * rsqrtf(x); }
+};
+
 // ------------------------------------------------------------------------
 // Linear acoustics, Sec. 3 Eq. acoustics with coefficients:
 //   p_t + K div u = 0,  rho u_t + grad p = 0.
@@ -73,7 +93,7 @@ struct Acoustics {
                                                  Waves<Real, NQ, NW>& w) {
         const Real dp = r.q[0] - l.q[0];
         const Real du = r.q[1] - l.q[1];
-        const Real inv = VAR ? Real(1) / (l.Z + r.Z) : P.inv2Z;
+        const Real inv = VAR ? Ops<Real>::rcp(l.Z + r.Z) : P.inv2Z;
         const Real a1 = (r.Z * du - dp) * inv;
         const Real a2 = (dp + l.Z * du) * inv;
         w.W[0][0] = -a1 * l.Z;
@@ -94,6 +114,11 @@ struct Acoustics {
                                                   Real s[NW]) {
         s[0] = -l.c;
         s[1] = r.c;
+    }
+
+    // max_p |s_p| of a solved interface.
+    __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) {
+        return fmax(-w.s[0], w.s[1]);
     }
 
     __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
@@ -119,7 +144,7 @@ struct ShallowWater {
     static constexpr int NW = 3;
     static constexpr int NA = 0;
     struct Params {
-        Real g, half_g;
+        Real g, sqrt_g;
     };
     struct Cell {
         Real q[NQ];
@@ -127,35 +152,54 @@ struct ShallowWater {
         Real sqh;    // sqrt(h)
         Real c;      // sqrt(g h)
     };
+    static constexpr bool kFast = sizeof(Real) == 4;
 
     __device__ __forceinline__ static int field(int d, int comp) {
         return comp == 0 ? 0 : (comp == 1 ? 1 + d : 2 - d);
     }
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
-        const Real rh = Real(1) / cell.q[0];
-        cell.u = cell.q[1] * rh;
-        cell.v = cell.q[2] * rh;
-        cell.sqh = sqrt(cell.q[0]);
-        cell.c = sqrt(P.g * cell.q[0]);
+        if constexpr (kFast) {
+            // one reciprocal square root gives sqrt(h) and 1/h
+            const Real r = rsqrtf(cell.q[0]);
+            const Real rh = r * r;
+            cell.sqh = cell.q[0] * r;
+            cell.u = cell.q[1] * rh;
+            cell.v = cell.q[2] * rh;
+            cell.c = P.sqrt_g * cell.sqh;
+        } else {
+            const Real rh = Real(1) / cell.q[0];
+            cell.u = cell.q[1] * rh;
+            cell.v = cell.q[2] * rh;
+            cell.sqh = sqrt(cell.q[0]);
+            cell.c = sqrt(P.g * cell.q[0]);
+        }
     }
 
+    // Roe averages; i2c = 1 / (2 c_hat).
     __device__ __forceinline__ static void roe(const Cell& l, const Cell& r, const Params& P,
-                                               Real& uh, Real& vh, Real& ch) {
-        const Real den = Real(1) / (l.sqh + r.sqh);
+                                               Real& uh, Real& vh, Real& ch, Real& i2c) {
+        const Real den = Ops<Real>::rcp(l.sqh + r.sqh);
         uh = (l.sqh * l.u + r.sqh * r.u) * den;
         vh = (l.sqh * l.v + r.sqh * r.v) * den;
-        ch = sqrt(P.g * (Real(0.5) * (l.q[0] + r.q[0])));
+        const Real gh = P.g * (Real(0.5) * (l.q[0] + r.q[0]));
+        if constexpr (kFast) {
+            const Real rc = rsqrtf(gh);
+            ch = gh * rc;
+            i2c = Real(0.5) * rc;
+        } else {
+            ch = sqrt(gh);
+            i2c = Real(0.5) / ch;
+        }
     }
 
     __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
                                                  Waves<Real, NQ, NW>& w) {
-        Real uh, vh, ch;
-        roe(l, r, P, uh, vh, ch);
+        Real uh, vh, ch, i2c;
+        roe(l, r, P, uh, vh, ch, i2c);
         const Real d0 = r.q[0] - l.q[0];
         const Real d1 = r.q[1] - l.q[1];
         const Real d2 = r.q[2] - l.q[2];
-        const Real i2c = Real(0.5) / ch;
         const Real s1 = uh - ch, s3 = uh + ch;
         const Real a1 = (s3 * d0 - d1) * i2c;
         const Real a2 = d2 - vh * d0;
@@ -183,8 +227,8 @@ struct ShallowWater {
             const Real hm = l.q[0] + w.W[0][0];
             const Real hum = l.q[1] + w.W[0][1];
             if (hm > Real(0) && hum > Real(0) && hum * hum > P.g * hm * hm * hm) {
-                const Real lam_m = hum / hm - sqrt(P.g * hm);
-                const Real beta = (lam_m - s1) / (lam_m - lam_l);
+                const Real lam_m = Ops<Real>::div(hum, hm) - Ops<Real>::sqrt_(P.g * hm);
+                const Real beta = Ops<Real>::div(lam_m - s1, lam_m - lam_l);
                 km1 = beta * lam_l;
                 kp1 = (Real(1) - beta) * lam_m;
             }
@@ -194,8 +238,8 @@ struct ShallowWater {
             const Real hm = r.q[0] - w.W[2][0];
             const Real hum = r.q[1] - w.W[2][1];
             if (hm > Real(0) && hum < Real(0) && hum * hum > P.g * hm * hm * hm) {
-                const Real lam_m = hum / hm + sqrt(P.g * hm);
-                const Real beta = (lam_r - s3) / (lam_r - lam_m);
+                const Real lam_m = Ops<Real>::div(hum, hm) + Ops<Real>::sqrt_(P.g * hm);
+                const Real beta = Ops<Real>::div(lam_r - s3, lam_r - lam_m);
                 km3 = beta * lam_m;
                 kp3 = (Real(1) - beta) * lam_r;
             }
@@ -209,11 +253,16 @@ struct ShallowWater {
 
     __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params& P,
                                                   Real s[NW]) {
-        Real uh, vh, ch;
-        roe(l, r, P, uh, vh, ch);
+        Real uh, vh, ch, i2c;
+        roe(l, r, P, uh, vh, ch, i2c);
         s[0] = uh - ch;
         s[1] = uh;
         s[2] = uh + ch;
+    }
+
+    // max_p |s_p| = max(|u_hat - c_hat|, |u_hat + c_hat|) (c_hat >= 0 bounds |u_hat|).
+    __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) {
+        return fmax(fabs(w.s[0]), fabs(w.s[2]));
     }
 
     __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {

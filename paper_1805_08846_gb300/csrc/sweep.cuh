@@ -14,13 +14,23 @@
 // register window of cells and waves.  Every interface's Riemann problem is
 // solved once per segment (plus three at the segment's ends), the limiter
 // reads the neighbouring interfaces' waves from registers, and the update of
-// a cell needs nothing from other threads, so there are no block barriers and
-// no shared-memory wave arrays (the paper's Sec. 5.1/5.3 machinery).  Waves
-// never reach global memory.  Lines along y or z are columns of adjacent x,
-// so a warp's loads and stores of one step are one contiguous row segment.
+// a cell needs nothing from other threads, so there are no shared wave
+// arrays (the paper's Sec. 5.1/5.3 machinery).  Waves never reach global
+// memory.
+//
+// Staging: the segment's cells arrive in chunks of C cells x kLines lines
+// per field, copied by bulk-tensor (TMA) loads into a ring of STAGES shared
+// memory buffers, several chunks ahead of the march, so the HBM stream is
+// deep enough without any per-thread prefetch registers.  For the y and z
+// sweeps a chunk is C rows of kLines consecutive x (one 512 B row per field
+// for FP32); for the x sweep it is kLines rows of C consecutive x, stored
+// with the 32-byte swizzle so that each thread's two 16-byte reads of its own
+// row are free of bank conflicts.  The two cells before and after the
+// segment (ghosts at the domain edge) are read directly.
 #pragma once
 #include "claw_types.cuh"
 #include "riemann.cuh"
+#include "tma.cuh"
 
 namespace claw {
 
@@ -88,42 +98,47 @@ __device__ __forceinline__ bool line_geometry(const TileDesc& td, const InstDesc
     }
 }
 
-template <class Sys, class Real, int LIM, int DIR, bool SPEEDS>
-__global__ void __launch_bounds__(kLines) sweep_kernel(const SweepArgs A, const typename Sys::Params P) {
-    using Cell = typename Sys::Cell;
-    using W = Waves<Real, Sys::NQ, Sys::NW>;
-    constexpr int NQ = Sys::NQ;
-    constexpr int NW = Sys::NW;
-    using SM = typename SpeedMax<Real>::T;
+// Warp max of the speed bits (integer max keeps NaN above +Inf), one atomic
+// per warp into the instance's control block; a non-physical flag likewise.
+template <int DIR, class SM>
+__device__ __forceinline__ void reduce_to_control(Control* ctl, SM smax, bool bad) {
+    unsigned long long m64 = widen_bits(smax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m64, o);
+        m64 = v > m64 ? v : m64;
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (m64) atomicMax(&ctl->smax[DIR], m64);
+        if (any_bad) atomicOr(&ctl->bad, 1u);
+    }
+}
 
+// ------------------------------------------------------------------------
+// Speeds-only pass (the CFL estimate of a new state): direct loads, no update.
+// ------------------------------------------------------------------------
+template <class Sys, class Real, int DIR>
+__global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const typename Sys::Params P) {
+    using Cell = typename Sys::Cell;
+    constexpr int NQ = Sys::NQ;
+    using SM = typename SpeedMax<Real>::T;
     const TileDesc td = A.tiles[blockIdx.x];
-    if (td.inst < A.inst_lo || td.inst >= A.inst_hi) return;
     const InstDesc& I = A.inst[td.inst];
     Control* ctl = A.ctl + td.inst;
-    if (!SPEEDS && *(volatile int*)&ctl->active == 0) return;
-
-    const int lane = threadIdx.x;
     long long base, stride;
-    const bool valid = line_geometry<DIR>(td, I, lane, base, stride);
+    const bool valid = line_geometry<DIR>(td, I, threadIdx.x, base, stride);
     const int N = I.n[DIR];
     const int bc_lo = I.bc[2 * DIR], bc_hi = I.bc[2 * DIR + 1];
-
     const Real* pool = static_cast<const Real*>(A.pool);
     const Real* qin[NQ];
-    Real* qout[NQ];
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
         const int f = Sys::field(DIR, c);
-        const int cur = ctl->cur[f];
-        const int sin = SPEEDS ? cur : (cur + A.slots.in_off[f]) % 3;
-        const int sout = (cur + A.slots.out_off[f]) % 3;
-        qin[c] = pool + I.offset + sin * I.vstride + f * I.fstride + base;
-        qout[c] = const_cast<Real*>(pool) + I.offset + sout * I.vstride + f * I.fstride + base;
+        qin[c] = pool + I.offset + ctl->cur[f] * I.vstride + f * I.fstride + base;
     }
     const Real* aux = nullptr;
     if (Sys::NA > 0) aux = static_cast<const Real*>(A.aux) + I.aux_offset + base;
-    const long long fstride = I.fstride;
-
     auto load = [&](int k, Cell& cell) {
         bool flip;
         const int j = map_cell(k, N, bc_lo, bc_hi, flip);
@@ -133,118 +148,308 @@ __global__ void __launch_bounds__(kLines) sweep_kernel(const SweepArgs A, const 
         if (flip) cell.q[1] = -cell.q[1];
         if constexpr (Sys::NA > 0) {
             cell.Z = __ldg(aux + o);
-            cell.c = __ldg(aux + fstride + o);
+            cell.c = __ldg(aux + I.fstride + o);
+        }
+        Sys::prepare(cell, P);
+    };
+    SM smax = 0;
+    if (valid) {
+        Cell cl, cr;
+        load(td.a - 1, cl);
+        for (int k = td.a; k <= td.b; ++k) {
+            load(k, cr);
+            Real s[Sys::NW];
+            Sys::speeds(cl, cr, P, s);
+#pragma unroll
+            for (int p = 0; p < Sys::NW; ++p) smax = max(smax, speed_bits(s[p]));
+            cl = cr;
+        }
+    }
+    reduce_to_control<DIR>(ctl, smax, false);
+}
+
+// ------------------------------------------------------------------------
+// The staged sweep.
+// ------------------------------------------------------------------------
+// Every plane box is 4 KB: 32 bytes of each of the 128 lines (x sweep) or
+// 4 KB / (128 * sizeof(Real)) cells of 128 adjacent lines (y, z sweeps).
+template <class Sys, class Real, int DIR>
+struct StageCfg {
+    static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
+    static constexpr int C = DIR == 0 ? 32 / (int)sizeof(Real) : 32 / (int)sizeof(Real);
+    static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
+    static constexpr int STAGES = 4;
+    static constexpr int STAGE_BYTES = NP * BOX;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
+    static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;   // register budget per thread
+};
+
+template <class Sys, class Real, int LIM, int DIR>
+__global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
+    sweep_kernel(const SweepArgs A, const typename Sys::Params P) {
+    using Cfg = StageCfg<Sys, Real, DIR>;
+    using Cell = typename Sys::Cell;
+    using W = Waves<Real, Sys::NQ, Sys::NW>;
+    constexpr int NQ = Sys::NQ;
+    constexpr int NW = Sys::NW;
+    constexpr int NA = Sys::NA;
+    constexpr int NP = Cfg::NP;
+    constexpr int C = Cfg::C;
+    constexpr int STAGES = Cfg::STAGES;
+    using SM = typename SpeedMax<Real>::T;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+
+    const TileDesc td = A.tiles[blockIdx.x];
+    if (td.inst < A.inst_lo || td.inst >= A.inst_hi) return;
+    const InstDesc& I = A.inst[td.inst];
+    Control* ctl = A.ctl + td.inst;
+    if (*(volatile int*)&ctl->active == 0) return;
+
+    const int lane = threadIdx.x;
+    long long base, stride;
+    const bool valid = line_geometry<DIR>(td, I, lane, base, stride);
+    const int N = I.n[DIR];
+    const int bc_lo = I.bc[2 * DIR], bc_hi = I.bc[2 * DIR + 1];
+    const int a = td.a, b = td.b;
+    const int nchunks = (b - a + C - 1) / C;
+
+    // Version slots: TMA plane index and direct pointers for each component.
+    Real* pool = static_cast<Real*>(A.pool);
+    int plane[NP];
+    const Real* qin[NQ];
+    Real* qout[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const int f = Sys::field(DIR, c);
+        const int cur = ctl->cur[f];
+        const int sin = (cur + A.slots.in_off[f]) % 3;
+        const int sout = (cur + A.slots.out_off[f]) % 3;
+        plane[c] = sin * A.m + f;
+        qin[c] = pool + I.offset + sin * I.vstride + f * I.fstride + base;
+        qout[c] = pool + I.offset + sout * I.vstride + f * I.fstride + base;
+    }
+#pragma unroll
+    for (int k = 0; k < NA; ++k) plane[NQ + k] = k;
+    const Real* aux = nullptr;
+    if (NA > 0) aux = static_cast<const Real*>(A.aux) + I.aux_offset + base;
+    const CUtensorMap* smap = &A.tma[td.inst].map[DIR];
+    const CUtensorMap* amap = &A.tma[td.inst].map[3 + DIR];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // Thread 0 issues chunk k into stage k % STAGES.
+    auto issue = [&](int k) {
+        const int s = k % STAGES;
+        const uint32_t bar = smem_addr(&bars[s]);
+        mbar_arrive_expect_tx(bar, Cfg::STAGE_BYTES);
+        const int pos = a + k * C;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const uint32_t dst = smem_addr(smem + s * Cfg::STAGE_BYTES + p * Cfg::BOX);
+            const CUtensorMap* map = p < NQ ? smap : amap;
+            if (DIR == 0) tma_load_3d(dst, map, bar, pos, td.line0, plane[p]);
+            else if (DIR == 1) tma_load_4d(dst, map, bar, td.line0, pos, td.other, plane[p]);
+            else tma_load_4d(dst, map, bar, td.line0, td.other, pos, plane[p]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES && k < nchunks; ++k) issue(k);
+    }
+
+    // Direct load of cell k (ghost or interior) for the segment's ends.
+    auto load_direct = [&](int k, Cell& cell) {
+        if (valid) {
+            bool flip;
+            const int j = map_cell(k, N, bc_lo, bc_hi, flip);
+            const long long o = (long long)j * stride;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) cell.q[c] = __ldg(qin[c] + o);
+            if (flip) cell.q[1] = -cell.q[1];
+            if constexpr (NA > 0) {
+                cell.Z = __ldg(aux + o);
+                cell.c = __ldg(aux + I.fstride + o);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) cell.q[c] = Real(1);
+            if constexpr (NA > 0) {
+                cell.Z = Real(1);
+                cell.c = Real(1);
+            }
         }
         Sys::prepare(cell, P);
     };
 
+    const Real nu = (Real)(ctl->dt_attempt / I.dx[DIR]);
     SM smax = 0;
     bool bad = false;
 
-    if (valid) {
-        const int a = td.a, b = td.b;
-        if constexpr (SPEEDS) {
-            // Speeds at interfaces a..b only (the CFL pass).
-            Cell cl, cr;
-            load(a - 1, cl);
-            for (int Iif = a; Iif <= b; ++Iif) {
-                load(Iif, cr);
-                Real s[NW];
-                Sys::speeds(cl, cr, P, s);
+    // March state: cell I-1 (prev), waves at interfaces I-2 (wA) and I-1 (wB),
+    // correction flux at I-2 (F0) and the kept state of cell I-2 (qkeep).
+    Cell prev;
+    W wA, wB;
+    Real F0[NQ], qkeep[NQ];
 #pragma unroll
-                for (int p = 0; p < NW; ++p) smax = max(smax, speed_bits(s[p]));
-                cl = cr;
-            }
-        } else {
-            const Real nu = (Real)(ctl->dt_attempt / I.dx[DIR]);
-            Cell cA, cB;          // cells I-1 and I of the newest interface I
-            W wA, wB, wC;         // waves at interfaces I-2, I-1, I
-            Real F0[NQ];          // correction flux at interface I-2
-            Real qkeep[NQ];       // kept state of cell I-2 (next to update)
+    for (int c = 0; c < NQ; ++c) F0[c] = qkeep[c] = Real(0);
 
-            load(a - 2, cA);
-            load(a - 1, cB);
-            Sys::solve(cA, cB, P, wA);          // interface a-1
-            cA = cB;
-            load(a, cB);
-            Sys::solve(cA, cB, P, wB);          // interface a
+    // Consume cell Iif (the interface between Iif-1 and Iif is solved).
+    auto advance = [&](int Iif, const Cell& cur) {
+        W wC;
+        Sys::solve(prev, cur, P, wC);
+        // lanes past the grid edge march over zero-filled copies: they write
+        // nothing and contribute no speed
+        if (valid && Iif >= a && Iif <= b) smax = max(smax, speed_bits(Sys::max_speed(wC)));
+        if (Iif >= a + 1) {
+            Real F1[NQ];
 #pragma unroll
-            for (int p = 0; p < NW; ++p) smax = max(smax, speed_bits(wB.s[p]));
+            for (int c = 0; c < NQ; ++c) F1[c] = Real(0);
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) {
-                qkeep[c] = cB.q[c];
-                F0[c] = Real(0);
-            }
-
-#pragma unroll 2
-            for (int Iif = a + 1; Iif <= b + 1; ++Iif) {
-                cA = cB;
-                load(Iif, cB);
-                Sys::solve(cA, cB, P, wC);      // interface Iif
-                if (Iif <= b) {
-#pragma unroll
-                    for (int p = 0; p < NW; ++p) smax = max(smax, speed_bits(wC.s[p]));
-                }
-                // Limited correction flux at interface Iif-1 (waves wB),
-                // the upwind wave taken from Iif-2 (wA) or Iif (wC).
-                Real F1[NQ];
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) F1[c] = Real(0);
-#pragma unroll
-                for (int p = 0; p < NW; ++p) {
-                    const Real sp = wB.s[p];
-                    Real phi = Real(1);
-                    if (LIM != kLimNone) {
-                        Real num = Real(0), den = Real(0);
-#pragma unroll
-                        for (int c = 0; c < NQ; ++c) {
-                            const Real up = sp > Real(0) ? wA.W[p][c] : wC.W[p][c];
-                            num += up * wB.W[p][c];
-                            den += wB.W[p][c] * wB.W[p][c];
-                        }
-                        phi = limiter_phi<LIM, Real>(num / den);
-                    }
-                    const Real as = fabs(sp);
-                    const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
-#pragma unroll
-                    for (int c = 0; c < NQ; ++c) F1[c] += k * wB.W[p][c];
-                }
-                // Update cell Iif-2 (its interfaces are Iif-2 and Iif-1).
-                if (Iif >= a + 2) {
-                    Real qn[NQ];
+            for (int p = 0; p < NW; ++p) {
+                const Real sp = wB.s[p];
+                Real phi = Real(1);
+                if (LIM != kLimNone) {
+                    Real num = Real(0), den = Real(0);
 #pragma unroll
                     for (int c = 0; c < NQ; ++c) {
-                        const Real first = wA.apdq[c] + wB.amdq[c];
-                        const Real second = F1[c] - F0[c];
-                        qn[c] = qkeep[c] - nu * first - nu * second;
-                        qout[c][(long long)(Iif - 2) * stride] = qn[c];
+                        const Real up = sp > Real(0) ? wA.W[p][c] : wC.W[p][c];
+                        num += up * wB.W[p][c];
+                        den += wB.W[p][c] * wB.W[p][c];
                     }
-                    bad |= Sys::nonphysical(qn);
+                    phi = limiter_phi<LIM, Real>(Ops<Real>::div(num, den));
                 }
+                const Real as = fabs(sp);
+                const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) F1[c] += k * wB.W[p][c];
+            }
+            if (Iif >= a + 2) {
+                Real qn[NQ];
 #pragma unroll
                 for (int c = 0; c < NQ; ++c) {
-                    qkeep[c] = cA.q[c];     // cell Iif-1, updated next iteration
-                    F0[c] = F1[c];
+                    const Real first = wA.apdq[c] + wB.amdq[c];
+                    const Real second = F1[c] - F0[c];
+                    qn[c] = qkeep[c] - nu * first - nu * second;
                 }
-                wA = wB;
-                wB = wC;
+                if (valid) {
+#pragma unroll
+                    for (int c = 0; c < NQ; ++c) qout[c][(long long)(Iif - 2) * stride] = qn[c];
+                    bad |= Sys::nonphysical(qn);
+                }
             }
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) F0[c] = F1[c];
         }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qkeep[c] = prev.q[c];
+        wA = wB;
+        wB = wC;
+        prev = cur;
+    };
+
+    {
+        Cell c0;
+        load_direct(a - 2, prev);
+        load_direct(a - 1, c0);
+        advance(a - 1, c0);
     }
 
-    // Warp max of the speed bits (integer max keeps NaN above +Inf), one
-    // atomic per warp into the instance's control block.
-    unsigned long long m64 = widen_bits(smax);
+    bool ok = true;
+    int kfail = nchunks;
+    for (int k = 0; k < nchunks; ++k) {
+        const int s = k % STAGES;
+        const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / STAGES) & 1));
+        const unsigned char* stage = smem + s * Cfg::STAGE_BYTES;
+        // Cells come straight from shared memory as they are marched over;
+        // the stage is released once the whole chunk has been consumed.
+        auto consume = [&](int j, const Real* vals) {
+            const int Iif = a + k * C + j;
+            if (Iif < b) {
+                Cell cur;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m64, o);
-        m64 = v > m64 ? v : m64;
+                for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
+                if constexpr (NA > 0) {
+                    cur.Z = vals[NQ];
+                    cur.c = vals[NQ + 1];
+                }
+                Sys::prepare(cur, P);
+                advance(Iif, cur);
+            }
+        };
+        if (DIR == 0) {
+            // row = lane, 32 bytes; the 16-byte halves are swapped on bit 2 of the row
+            constexpr int H = 16 / (int)sizeof(Real);     // cells per half row
+            const int sw = (lane >> 2) & 1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                Real hv[NP][H];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const unsigned char* row = stage + p * Cfg::BOX + lane * 32 + 16 * (h ^ sw);
+                    if constexpr (sizeof(Real) == 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(row);
+                        hv[p][0] = t.x; hv[p][1] = t.y; hv[p][2] = t.z; hv[p][3] = t.w;
+                    } else {
+                        const double2 t = *reinterpret_cast<const double2*>(row);
+                        hv[p][0] = t.x; hv[p][1] = t.y;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < H; ++j) {
+                    Real vals[NP];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) vals[p] = hv[p][j];
+                    consume(h * H + j, vals);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                Real vals[NP];
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    vals[p] = reinterpret_cast<const Real*>(stage + p * Cfg::BOX)[j * kLines + lane];
+                consume(j, vals);
+            }
+        }
+        // Every thread is done with stage s: it may be refilled.  The vote
+        // makes a timed-out wait a uniform decision of the CTA (the chunk's
+        // results then land in a version slot that is never kept).
+        ok = __syncthreads_and(arrived) != 0;
+        if (!ok) {
+            kfail = k;
+            break;
+        }
+        if (threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
     }
-    const bool any_bad = __any_sync(0xffffffffu, bad);
-    if ((lane & 31) == 0) {
-        if (m64) atomicMax(&ctl->smax[DIR], m64);
-        if (any_bad) atomicOr(&ctl->bad, 1u);
+
+    if (!ok) {
+        // A copy never arrived: record it, wait (bounded) for the copies still
+        // in flight into this CTA's shared memory, and leave.
+        if (threadIdx.x == 0) {
+            atomicOr(&ctl->status, kStatTimeout);
+            // chunks kfail .. kfail + STAGES - 1 were issued and not consumed
+            for (int k = kfail; k < kfail + STAGES && k < nchunks; ++k)
+                mbar_wait_bounded(smem_addr(&bars[k % STAGES]), (uint32_t)((k / STAGES) & 1));
+        }
+        return;
     }
+
+    {
+        Cell c1;
+        load_direct(b, c1);
+        advance(b, c1);
+        load_direct(b + 1, c1);
+        advance(b + 1, c1);
+    }
+    reduce_to_control<DIR>(ctl, smax, bad);
 }
 
 }  // namespace claw

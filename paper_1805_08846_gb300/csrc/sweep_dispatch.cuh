@@ -6,20 +6,35 @@
 
 namespace claw {
 
-template <class Sys, class Real, int LIM, int DIR, bool SPEEDS>
+template <class Sys, class Real, int LIM, int DIR>
 cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     if (L.grid == 0) return cudaSuccess;
-    sweep_kernel<Sys, Real, LIM, DIR, SPEEDS><<<L.grid, kLines, 0, L.stream>>>(L.args, P);
+    using Cfg = StageCfg<Sys, Real, DIR>;
+    static bool smem_set = false;   // idempotent, so a racing second set is harmless
+    if (!smem_set) {
+        const cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        smem_set = true;
+    }
+    sweep_kernel<Sys, Real, LIM, DIR><<<L.grid, kLines, Cfg::SMEM, L.stream>>>(L.args, P);
+    return cudaGetLastError();
+}
+
+template <class Sys, class Real, int DIR>
+cudaError_t speed_go(const SweepLaunch& L, const typename Sys::Params& P) {
+    if (L.grid == 0) return cudaSuccess;
+    speed_kernel<Sys, Real, DIR><<<L.grid, kLines, 0, L.stream>>>(L.args, P);
     return cudaGetLastError();
 }
 
 template <class Sys, class Real, int DIR>
 cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P) {
-    if (L.speeds) return sweep_go<Sys, Real, kLimNone, DIR, true>(L, P);
+    if (L.speeds) return speed_go<Sys, Real, DIR>(L, P);
     switch (L.limiter) {
-        case kLimNone: return sweep_go<Sys, Real, kLimNone, DIR, false>(L, P);
-        case kLimMinmod: return sweep_go<Sys, Real, kLimMinmod, DIR, false>(L, P);
-        default: return sweep_go<Sys, Real, kLimMC, DIR, false>(L, P);
+        case kLimNone: return sweep_go<Sys, Real, kLimNone, DIR>(L, P);
+        case kLimMinmod: return sweep_go<Sys, Real, kLimMinmod, DIR>(L, P);
+        default: return sweep_go<Sys, Real, kLimMC, DIR>(L, P);
     }
 }
 

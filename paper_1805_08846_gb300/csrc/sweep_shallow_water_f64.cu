@@ -1,10 +1,12 @@
 // Sweep kernels: shallow water (Roe + Harten-Hyman), double, 2D only.
+#include <math.h>
+
 #include "sweep_dispatch.cuh"
 
 namespace claw {
 cudaError_t launch_sweep_shallow_water_f64(const SweepLaunch& L) {
     using S = ShallowWater<double>;
-    const S::Params P{(double)L.args.g, (double)(0.5 * L.args.g)};
+    const S::Params P{(double)L.args.g, (double)sqrt(L.args.g)};
     return sweep_by_dir<S, double, false>(L, P);
 }
 }  // namespace claw
