@@ -117,15 +117,23 @@ claw_status build_tiles(claw_solver* s) {
             const InstDesc& I = s->inst[i];
             const int lo = (int)T.size();
             const int N = I.n[d];
+            // Segments [a, b) of length L; a tail shorter than 2 cells joins
+            // the segment before it (the sweep kernel needs b - a >= 2).
+            std::vector<std::pair<int, int>> segs;
+            for (int a = 0; a < N; a += L) segs.push_back({a, std::min(a + L, N)});
+            if (segs.size() > 1 && segs.back().second - segs.back().first < 2) {
+                segs[segs.size() - 2].second = N;
+                segs.pop_back();
+            }
             if (d == 0) {
                 const int rows = I.n[1] * I.n[2];
                 for (int r0 = 0; r0 < rows; r0 += kLines)
-                    for (int a = 0; a < N; a += L) T.push_back({i, r0, 0, a, std::min(a + L, N), {0, 0, 0}});
+                    for (auto& sg : segs) T.push_back({i, r0, 0, sg.first, sg.second, {0, 0, 0}});
             } else {
                 const int others = (d == 1) ? I.n[2] : I.n[1];
                 for (int o = 0; o < others; ++o)
                     for (int x0 = 0; x0 < I.n[0]; x0 += kLines)
-                        for (int a = 0; a < N; a += L) T.push_back({i, x0, o, a, std::min(a + L, N), {0, 0, 0}});
+                        for (auto& sg : segs) T.push_back({i, x0, o, sg.first, sg.second, {0, 0, 0}});
             }
             s->inst_tiles[d][i] = {lo, (int)T.size()};
         }

@@ -173,14 +173,18 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
 // ------------------------------------------------------------------------
 // Every plane box is 4 KB: 32 bytes of each of the 128 lines (x sweep) or
 // 4 KB / (128 * sizeof(Real)) cells of 128 adjacent lines (y, z sweeps).
+// The x sweep also stages its results: OUTBUF boxes per touched field, each
+// written back by one bulk-tensor store once its C cells are final.
 template <class Sys, class Real, int DIR>
 struct StageCfg {
     static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
-    static constexpr int C = DIR == 0 ? 32 / (int)sizeof(Real) : 32 / (int)sizeof(Real);
+    static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
     static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = DIR == 0 ? 3 : 4;
     static constexpr int STAGE_BYTES = NP * BOX;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
+    static constexpr int OUTBUF = DIR == 0 ? 3 : 0;
+    static constexpr int OUT_BYTES = OUTBUF * Sys::NQ * BOX;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + OUT_BYTES + 1024 + 64;  // + alignment, barriers
     static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;   // register budget per thread
 };
 
@@ -201,7 +205,8 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+    unsigned char* outbox = smem + STAGES * Cfg::STAGE_BYTES;   // x sweep: result boxes
+    uint64_t* bars = reinterpret_cast<uint64_t*>(outbox + Cfg::OUT_BYTES);
 
     const TileDesc td = A.tiles[blockIdx.x];
     if (td.inst < A.inst_lo || td.inst >= A.inst_hi) return;
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
 
     // Version slots: TMA plane index and direct pointers for each component.
     Real* pool = static_cast<Real*>(A.pool);
-    int plane[NP];
+    int plane[NP], plane_out[NQ];
     const Real* qin[NQ];
     Real* qout[NQ];
 #pragma unroll
@@ -229,6 +234,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         const int sin = (cur + A.slots.in_off[f]) % 3;
         const int sout = (cur + A.slots.out_off[f]) % 3;
         plane[c] = sin * A.m + f;
+        plane_out[c] = sout * A.m + f;
         qin[c] = pool + I.offset + sin * I.vstride + f * I.fstride + base;
         qout[c] = pool + I.offset + sout * I.vstride + f * I.fstride + base;
     }
@@ -292,96 +298,155 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     SM smax = 0;
     bool bad = false;
 
-    // March state: cell I-1 (prev), waves at interfaces I-2 (wA) and I-1 (wB),
-    // correction flux at I-2 (F0) and the kept state of cell I-2 (qkeep).
+    // March state after interface I (between cells I-1 and I) is solved:
+    //   prev   cell I (with its per-cell precomputation)
+    //   wB     waves, speeds and fluctuations at interface I
+    //   ssB    W_p . W_p at I;  dAB  W_p(I-1) . W_p(I)  (limiter ratios)
+    //   apdqA  A+dQ at interface I-1
+    //   F0     correction flux at interface I-1;  qkeep  state of cell I-1
     Cell prev;
-    W wA, wB;
-    Real F0[NQ], qkeep[NQ];
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) F0[c] = qkeep[c] = Real(0);
+    W wB;
+    Real ssB[NW], dAB[NW], apdqA[NQ], F0[NQ], qkeep[NQ];
 
-    // Consume cell Iif (the interface between Iif-1 and Iif is solved).
-    auto advance = [&](int Iif, const Cell& cur) {
+    auto dot = [](const W& x, const W& y, int p) {
+        Real d = Real(0);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) d += x.W[p][c] * y.W[p][c];
+        return d;
+    };
+    // Limited correction flux at interface I (waves wB, ratios from the
+    // upwind side: I-1 when s > 0, else I+1).
+    auto flux = [&](const Real* d_up_left, const Real* d_up_right, Real* F) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) F[c] = Real(0);
+#pragma unroll
+        for (int p = 0; p < NW; ++p) {
+            const Real sp = wB.s[p];
+            Real phi = Real(1);
+            if (LIM != kLimNone) {
+                const Real num = sp > Real(0) ? d_up_left[p] : d_up_right[p];
+                phi = limiter_phi<LIM, Real>(Ops<Real>::div(num, ssB[p]));
+            }
+            const Real as = fabs(sp);
+            const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) F[c] += k * wB.W[p][c];
+        }
+    };
+    // Consume cell I+1: solve interface I+1, limit interface I, update cell
+    // I-1 (out of place).  SPEED: interface I+1 bounds an interior cell of
+    // the segment.  UPDATE: cell I-1 belongs to the segment.
+    auto step = [&](const Cell& cur, bool speed, bool update, long long cell_off) {
         W wC;
         Sys::solve(prev, cur, P, wC);
-        // lanes past the grid edge march over zero-filled copies: they write
-        // nothing and contribute no speed
-        if (valid && Iif >= a && Iif <= b) smax = max(smax, speed_bits(Sys::max_speed(wC)));
-        if (Iif >= a + 1) {
-            Real F1[NQ];
+        if (valid && speed) smax = max(smax, speed_bits(Sys::max_speed(wC)));
+        Real dBC[NW], ssC[NW];
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) F1[c] = Real(0);
+        for (int p = 0; p < NW; ++p) {
+            dBC[p] = dot(wB, wC, p);
+            ssC[p] = dot(wC, wC, p);
+        }
+        Real F1[NQ];
+        flux(dAB, dBC, F1);
+        if (update) {
+            Real qn[NQ];
 #pragma unroll
-            for (int p = 0; p < NW; ++p) {
-                const Real sp = wB.s[p];
-                Real phi = Real(1);
-                if (LIM != kLimNone) {
-                    Real num = Real(0), den = Real(0);
-#pragma unroll
-                    for (int c = 0; c < NQ; ++c) {
-                        const Real up = sp > Real(0) ? wA.W[p][c] : wC.W[p][c];
-                        num += up * wB.W[p][c];
-                        den += wB.W[p][c] * wB.W[p][c];
-                    }
-                    phi = limiter_phi<LIM, Real>(Ops<Real>::div(num, den));
-                }
-                const Real as = fabs(sp);
-                const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) F1[c] += k * wB.W[p][c];
+            for (int c = 0; c < NQ; ++c) {
+                const Real first = apdqA[c] + wB.amdq[c];
+                const Real second = F1[c] - F0[c];
+                qn[c] = qkeep[c] - nu * first - nu * second;
             }
-            if (Iif >= a + 2) {
-                Real qn[NQ];
+            if (DIR == 0) {
+                // cell_off is the cell index along x: its column in result box
+                // (cell - a) / C, with the same 32-byte swizzle as the inputs
+                const int rel = (int)cell_off - a;
+                unsigned char* box = outbox + ((rel / C) % Cfg::OUTBUF) * (NQ * Cfg::BOX);
+                const int col = rel % C;
+                const int byte = ((((col * (int)sizeof(Real)) >> 4) ^ ((lane >> 2) & 1)) << 4) +
+                                 ((col * (int)sizeof(Real)) & 15);
 #pragma unroll
-                for (int c = 0; c < NQ; ++c) {
-                    const Real first = wA.apdq[c] + wB.amdq[c];
-                    const Real second = F1[c] - F0[c];
-                    qn[c] = qkeep[c] - nu * first - nu * second;
-                }
-                if (valid) {
+                for (int c = 0; c < NQ; ++c)
+                    *reinterpret_cast<Real*>(box + c * Cfg::BOX + lane * 32 + byte) = qn[c];
+                if (valid) bad |= Sys::nonphysical(qn);
+            } else if (valid) {
 #pragma unroll
-                    for (int c = 0; c < NQ; ++c) qout[c][(long long)(Iif - 2) * stride] = qn[c];
-                    bad |= Sys::nonphysical(qn);
-                }
+                for (int c = 0; c < NQ; ++c) qout[c][cell_off] = qn[c];
+                bad |= Sys::nonphysical(qn);
             }
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) F0[c] = F1[c];
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) qkeep[c] = prev.q[c];
-        wA = wB;
+        for (int c = 0; c < NQ; ++c) {
+            F0[c] = F1[c];
+            apdqA[c] = wB.apdq[c];
+            qkeep[c] = prev.q[c];
+        }
+#pragma unroll
+        for (int p = 0; p < NW; ++p) {
+            dAB[p] = dBC[p];
+            ssB[p] = ssC[p];
+        }
         wB = wC;
         prev = cur;
     };
 
+    // Prologue (direct loads): cells a-2 .. a+1; interfaces a-1, a, a+1;
+    // flux at a.  Needs b - a >= 2 (the tile builder guarantees it).
     {
-        Cell c0;
-        load_direct(a - 2, prev);
-        load_direct(a - 1, c0);
-        advance(a - 1, c0);
+        Cell c0, c1;
+        W wX;
+        load_direct(a - 2, c0);
+        load_direct(a - 1, c1);
+        Sys::solve(c0, c1, P, wX);                    // interface a-1
+        load_direct(a, c0);
+        Sys::solve(c1, c0, P, wB);                    // interface a
+        if (valid) smax = max(smax, speed_bits(Sys::max_speed(wB)));
+#pragma unroll
+        for (int p = 0; p < NW; ++p) {
+            dAB[p] = dot(wX, wB, p);
+            ssB[p] = dot(wB, wB, p);
+        }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            F0[c] = Real(0);
+            apdqA[c] = wX.apdq[c];
+            qkeep[c] = c1.q[c];
+        }
+        prev = c0;                                     // cell a
+        load_direct(a + 1, c1);
+        step(c1, true, false, 0);            // interface a+1, flux at a
     }
+
+    // x sweep: bulk-store result box of output chunk ko (cells a+ko*C ..).
+    auto store_out = [&](int ko) {
+        const unsigned char* box = outbox + (ko % Cfg::OUTBUF) * (NQ * Cfg::BOX);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c)
+            tma_store_3d(smap, smem_addr(box + c * Cfg::BOX), a + ko * C, td.line0, plane_out[c]);
+        bulk_commit();
+    };
 
     bool ok = true;
     int kfail = nchunks;
+    int stored = 0;        // x sweep: result boxes already written back
     for (int k = 0; k < nchunks; ++k) {
         const int s = k % STAGES;
         const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / STAGES) & 1));
         const unsigned char* stage = smem + s * Cfg::STAGE_BYTES;
+        const int jlo = k == 0 ? 2 : 0;                // cells a, a+1 came directly
+        const int jhi = min(C, b - (a + k * C));       // cells from b on come directly
         // Cells come straight from shared memory as they are marched over;
         // the stage is released once the whole chunk has been consumed.
         auto consume = [&](int j, const Real* vals) {
             const int Iif = a + k * C + j;
-            if (Iif < b) {
-                Cell cur;
+            Cell cur;
 #pragma unroll
-                for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
-                if constexpr (NA > 0) {
-                    cur.Z = vals[NQ];
-                    cur.c = vals[NQ + 1];
-                }
-                Sys::prepare(cur, P);
-                advance(Iif, cur);
+            for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
+            if constexpr (NA > 0) {
+                cur.Z = vals[NQ];
+                cur.c = vals[NQ + 1];
             }
+            Sys::prepare(cur, P);
+            step(cur, true, true, (long long)(Iif - 2) * stride);
         };
         if (DIR == 0) {
             // row = lane, 32 bytes; the 16-byte halves are swapped on bit 2 of the row
@@ -403,21 +468,31 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
                 }
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
-                    Real vals[NP];
+                    const int jj = h * H + j;
+                    if (jj >= jlo && jj < jhi) {
+                        Real vals[NP];
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) vals[p] = hv[p][j];
-                    consume(h * H + j, vals);
+                        for (int p = 0; p < NP; ++p) vals[p] = hv[p][j];
+                        consume(jj, vals);
+                    }
                 }
             }
         } else {
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
+#pragma unroll 2
+            for (int j = jlo; j < jhi; ++j) {
                 Real vals[NP];
 #pragma unroll
                 for (int p = 0; p < NP; ++p)
                     vals[p] = reinterpret_cast<const Real*>(stage + p * Cfg::BOX)[j * kLines + lane];
                 consume(j, vals);
             }
+        }
+        if (DIR == 0) {
+            // result writes -> async proxy; the store that last used the box the
+            // next chunk starts filling (OUTBUF = 3: issued one chunk ago) must
+            // have finished reading it
+            fence_proxy_async_smem();
+            if (threadIdx.x == 0) bulk_wait_read<0>();
         }
         // Every thread is done with stage s: it may be refilled.  The vote
         // makes a timed-out wait a uniform decision of the CTA (the chunk's
@@ -426,6 +501,13 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         if (!ok) {
             kfail = k;
             break;
+        }
+        // Result box k-1 got its last two cells from cells j = 0, 1 of this
+        // chunk -- unless the chunk holds fewer than two cells, in which case
+        // they come from the epilogue and the box is written back after it.
+        if (DIR == 0 && k >= 1 && b - (a + k * C) >= 2) {
+            if (threadIdx.x == 0) store_out(k - 1);
+            stored = k;
         }
         if (threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
     }
@@ -438,16 +520,28 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             // chunks kfail .. kfail + STAGES - 1 were issued and not consumed
             for (int k = kfail; k < kfail + STAGES && k < nchunks; ++k)
                 mbar_wait_bounded(smem_addr(&bars[k % STAGES]), (uint32_t)((k / STAGES) & 1));
+            if (DIR == 0) bulk_wait_all();
         }
         return;
     }
 
+    // Epilogue (direct loads): cells b, b+1; the last interface b+1 bounds no
+    // interior cell of the segment.
     {
         Cell c1;
         load_direct(b, c1);
-        advance(b, c1);
+        step(c1, true, true, (long long)(b - 2) * stride);
         load_direct(b + 1, c1);
-        advance(b + 1, c1);
+        step(c1, false, true, (long long)(b - 1) * stride);
+    }
+    if (DIR == 0) {
+        // the remaining result boxes (a tail past b is the grid edge: clipped)
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int ko = stored; ko < nchunks; ++ko) store_out(ko);
+            bulk_wait_all();
+        }
     }
     reduce_to_control<DIR>(ctl, smax, bad);
 }

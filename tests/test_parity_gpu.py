@@ -67,7 +67,13 @@ CASES += [("acoustics", (130, 67), "mc", ("wall", "extrap", "periodic", "wall"))
           ("acoustics_var", (23, 19, 21), "mc", "wall"),
           ("acoustics_var", (40, 9, 7), "minmod", ("periodic", "periodic", "extrap", "wall", "wall", "extrap")),
           ("acoustics", (17, 21, 25), "none", "periodic"),
-          ("acoustics_var", (150, 20), "mc", "periodic")]
+          ("acoustics_var", (150, 20), "mc", "periodic"),
+          # x extents whose last segment ends with a one-cell chunk (73) or
+          # whose one-cell tail joins the segment before it (129)
+          ("shallow_water", (73, 20), "mc", "periodic"),
+          ("acoustics", (129, 11), "minmod", "wall"),
+          ("shallow_water", (2, 5), "minmod", "wall"),
+          ("acoustics_var", (3, 2, 2), "mc", "periodic")]
 
 
 @pytest.mark.parametrize("system,shape,limiter,bc", CASES)
