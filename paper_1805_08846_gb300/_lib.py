@@ -68,6 +68,7 @@ _SIGS = {
     "claw_ensemble_size": [_vp],
     "claw_profile_steps": [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_long)],
     "claw_set_segment": [_vp, C.c_int, C.c_int],
+    "claw_autotune": [_vp, C.c_int, C.POINTER(C.c_int)],
     "claw_max_speed_noalloc": [C.POINTER(claw_grid), C.c_int, C.POINTER(C.c_int),
                                C.POINTER(claw_params), _vp, _vp, _vp, _vp, _vp],
 }
@@ -289,6 +290,12 @@ def claw_profile_steps(h, nsteps):
 
 def claw_set_segment(h, d, seg_len):
     _check(lib().claw_set_segment(h, int(d), int(seg_len)), "claw_set_segment")
+
+
+def claw_autotune(h, trial_steps=3):
+    seg = (C.c_int * 3)()
+    _check(lib().claw_autotune(h, int(trial_steps), seg), "claw_autotune")
+    return list(seg)
 
 
 def claw_max_speed_noalloc(n, dx, system, bc, params, q_dev, out_dev, rho_dev=None, K_dev=None,

@@ -69,6 +69,9 @@ struct claw_solver {
     void* aux = nullptr;
     double* stage = nullptr;
     double* d_sums = nullptr;
+    int* d_counters = nullptr;          // persistent tile schedule, one per direction
+    int* d_order[3] = {nullptr, nullptr, nullptr};
+    bool persistent = true;
     size_t stage_elems = 0;
     int seg[3] = {64, 64, 64};
     std::vector<TileDesc> tiles[3];
@@ -141,6 +144,21 @@ claw_status build_tiles(claw_solver* s) {
         s->d_tiles[d] = nullptr;
         CK(cudaMalloc(&s->d_tiles[d], sizeof(TileDesc) * std::max<size_t>(T.size(), 1)));
         CK(cudaMemcpy(s->d_tiles[d], T.data(), sizeof(TileDesc) * T.size(), cudaMemcpyHostToDevice));
+        // Visiting order of the persistent sweep: most cells first (longest
+        // processing time first balances uneven instances), stable.
+        std::vector<int> order(T.size());
+        for (size_t t = 0; t < T.size(); ++t) order[t] = (int)t;
+        auto cells = [&](const TileDesc& td) {
+            const InstDesc& I = s->inst[td.inst];
+            const int nl = d == 0 ? I.n[1] * I.n[2] : I.n[0];
+            return (long long)std::min(kLines, nl - td.line0) * (td.b - td.a);
+        };
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return cells(T[x]) > cells(T[y]); });
+        if (s->d_order[d]) cudaFree(s->d_order[d]);
+        s->d_order[d] = nullptr;
+        CK(cudaMalloc(&s->d_order[d], sizeof(int) * std::max<size_t>(order.size(), 1)));
+        CK(cudaMemcpy(s->d_order[d], order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     return CLAW_OK;
 }
@@ -148,6 +166,10 @@ claw_status build_tiles(claw_solver* s) {
 SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi) {
     SweepArgs a{};
     a.tiles = s->d_tiles[d] + tile_lo;
+    const bool whole = tile_lo == 0 && tile_hi == (int)s->tiles[d].size();
+    a.order = whole ? s->d_order[d] : nullptr;
+    a.tile_counter = s->d_counters + d;
+    a.persistent = whole && s->persistent;
     a.ntiles = tile_hi - tile_lo;
     a.inst = s->d_inst;
     a.tma = s->d_tma;
@@ -182,7 +204,7 @@ claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, 
 // the step-control kernel.
 claw_status enqueue_attempt(claw_solver* s) {
     for (int d = 0; d < s->ndim; ++d) CKS(launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false));
-    CK(launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->stream));
+    CK(launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->d_counters, s->stream));
     return CLAW_OK;
 }
 
@@ -424,6 +446,8 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     s->stage_elems = max_cells * m;
     CK(cudaMalloc(&s->stage, s->stage_elems * sizeof(double)));
     CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
+    CK(cudaMalloc(&s->d_counters, 4 * sizeof(int)));
+    CK(cudaMemsetAsync(s->d_counters, 0, 4 * sizeof(int), s->stream));
     CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
     CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
     {
@@ -582,8 +606,11 @@ void claw_destroy(claw_solver* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     free_graphs(s);
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
         if (s->d_tiles[d]) cudaFree(s->d_tiles[d]);
+        if (s->d_order[d]) cudaFree(s->d_order[d]);
+    }
+    if (s->d_counters) cudaFree(s->d_counters);
     if (s->pool) cudaFree(s->pool);
     if (s->aux) cudaFree(s->aux);
     if (s->stage) cudaFree(s->stage);
@@ -614,7 +641,7 @@ int claw_ensemble_size(const claw_solver* s) { return s ? s->B : 0; }
 
 claw_status claw_step(claw_solver* s, double dt, double* cfl_out) {
     CKS(check_solver(s));
-    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, 1, 0.0, dt > 0.0 ? dt : 0.0, 0.0, s->stream));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, 1, 0.0, dt > 0.0 ? dt : 0.0, 0.0, s->d_counters, s->stream));
     CKS(run_armed(s, kModeSteps, 1));
     if (cfl_out) *cfl_out = s->h_ctl[0].cfl_last;
     return CLAW_OK;
@@ -624,7 +651,7 @@ claw_status claw_run_steps(claw_solver* s, int nsteps) {
     CKS(check_solver(s));
     if (nsteps < 0) return fail(CLAW_EINVAL, "nsteps < 0");
     if (nsteps == 0) return CLAW_OK;
-    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->stream));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->d_counters, s->stream));
     return run_armed(s, kModeSteps, nsteps);
 }
 
@@ -636,7 +663,7 @@ claw_status claw_advance(claw_solver* s, double t_final, double cfl_target, int*
     const double t0 = s->h_ctl[0].t;
     const long long n0 = s->h_ctl[0].nacc;
     if (!(t_final >= t0)) return fail(CLAW_EINVAL, "t_final %.17g is before the current time %.17g", t_final, t0);
-    CK(launch_arm(s->d_ctl, 0, s->B, kModeTFinal, 0, t_final, 0.0, cfl_target > 0.0 ? cfl_target : 0.0, s->stream));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeTFinal, 0, t_final, 0.0, cfl_target > 0.0 ? cfl_target : 0.0, s->d_counters, s->stream));
     claw_status st = run_armed(s, kModeTFinal, 0);
     if (nsteps_out) *nsteps_out = (int)(s->h_ctl[0].nacc - n0);
     return st;
@@ -701,6 +728,57 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
     return build_tiles(s);
 }
 
+claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
+    CKS(check_solver(s));
+    if (trial_steps < 1) return fail(CLAW_EINVAL, "trial_steps must be >= 1");
+    // Save the state pool and the control blocks; every trial runs from them.
+    size_t pool_bytes = 0;
+    for (int i = 0; i < s->B; ++i)
+        pool_bytes = std::max(pool_bytes, (size_t)((s->inst[i].offset + 3 * s->inst[i].vstride) * s->esize));
+    void* saved = nullptr;
+    Control* saved_ctl = nullptr;
+    CK(cudaMalloc(&saved, pool_bytes));
+    CK(cudaMalloc(&saved_ctl, sizeof(Control) * s->B));
+    CK(cudaMemcpyAsync(saved, s->pool, pool_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(saved_ctl, s->d_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToDevice, s->stream));
+    auto restore = [&]() -> claw_status {
+        CK(cudaMemcpyAsync(s->pool, saved, pool_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->d_ctl, saved_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToDevice, s->stream));
+        return CLAW_OK;
+    };
+    static const int cand_x[] = {16, 32, 48, 64, 96, 128, 192, 256, 512};
+    static const int cand_t[] = {8, 16, 24, 32, 48, 64, 96, 128, 256};
+    int best[3] = {s->seg[0], s->seg[1], s->seg[2]};
+    claw_status st = CLAW_OK;
+    for (int d = 0; d < s->ndim && st == CLAW_OK; ++d) {
+        const int* cand = d == 0 ? cand_x : cand_t;
+        double best_ms = 1e30;
+        for (int k = 0; k < 9 && st == CLAW_OK; ++k) {
+            int maxN = 0;
+            for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[d]);
+            if (cand[k] > 2 * maxN && k > 0) break;
+            st = claw_set_segment(s, d, cand[k]);
+            if (st != CLAW_OK) break;
+            double ms[4], tot;
+            long nl;
+            st = claw_profile_steps(s, trial_steps, ms, &tot, &nl);
+            if (st == CLAW_OK && ms[d] < best_ms) {
+                best_ms = ms[d];
+                best[d] = s->seg[d];
+            }
+            if (st == CLAW_OK) st = restore();
+        }
+        if (st == CLAW_OK) st = claw_set_segment(s, d, best[d]);
+    }
+    cudaStreamSynchronize(s->stream);
+    cudaFree(saved);
+    cudaFree(saved_ctl);
+    if (st != CLAW_OK) return st;
+    if (seg_out)
+        for (int d = 0; d < 3; ++d) seg_out[d] = s->seg[d];
+    return CLAW_OK;
+}
+
 claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], double* total_ms,
                                long* launches) {
     CKS(check_solver(s));
@@ -711,7 +789,7 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
     cudaEvent_t t0, t1;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));
-    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->stream));
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, 0.0, 0.0, s->d_counters, s->stream));
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     claw_status st = CLAW_OK;
@@ -722,7 +800,7 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
             // not just capture dependencies.
             cudaEventRecordWithFlags(e[0], s->stream, cudaEventRecordExternal);
             if (d < s->ndim) st = launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false);
-            else if (launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->stream) != cudaSuccess)
+            else if (launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->d_counters, s->stream) != cudaSuccess)
                 st = fail(CLAW_ECUDA, "finish launch failed");
             cudaEventRecordWithFlags(e[1], s->stream, cudaEventRecordExternal);
         }

@@ -93,6 +93,9 @@ struct alignas(64) TmaSet {
 
 struct SweepArgs {
     const TileDesc* tiles;
+    const int* order;      // tile visiting order (largest first), or null
+    int* tile_counter;     // persistent schedule: next tile to take
+    int persistent;
     const TmaSet* tma;
     const InstDesc* inst;
     Control* ctl;

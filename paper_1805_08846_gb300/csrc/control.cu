@@ -45,8 +45,9 @@ __device__ __forceinline__ void prepare_attempt(Control& c) {
 }
 
 __global__ void arm_kernel(Control* ctl, int lo, int hi, int mode, long long nsteps,
-                           double t_final, double fixed_dt, double cfl_desired) {
+                           double t_final, double fixed_dt, double cfl_desired, int* counters) {
     const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == lo && counters) counters[0] = counters[1] = counters[2] = 0;
     if (i >= hi) return;
     Control& c = ctl[i];
     if (cfl_desired > 0.0 && cfl_desired != c.cfl_desired) {
@@ -63,8 +64,11 @@ __global__ void arm_kernel(Control* ctl, int lo, int hi, int mode, long long nst
     prepare_attempt(c);
 }
 
-__global__ void finish_kernel(Control* ctl, const InstDesc* inst, int lo, int hi, FinalSlots fs) {
+__global__ void finish_kernel(Control* ctl, const InstDesc* inst, int lo, int hi, FinalSlots fs,
+                              int* counters) {
     const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    // the sweeps of this attempt are done: rewind their tile schedules
+    if (i == lo && counters) counters[0] = counters[1] = counters[2] = 0;
     if (i >= hi) return;
     Control& c = ctl[i];
     if (!c.active) return;
@@ -144,19 +148,19 @@ __global__ void reset_status_kernel(Control* ctl, int i) {
 }
 
 cudaError_t launch_arm(Control* ctl, int lo, int hi, int mode, long long nsteps, double t_final,
-                       double fixed_dt, double cfl_desired, cudaStream_t st) {
+                       double fixed_dt, double cfl_desired, int* counters, cudaStream_t st) {
     const int n = hi - lo;
     if (n <= 0) return cudaSuccess;
     arm_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctl, lo, hi, mode, nsteps, t_final, fixed_dt,
-                                                cfl_desired);
+                                                cfl_desired, counters);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish(Control* ctl, const InstDesc* inst, int lo, int hi, FinalSlots fs,
-                          cudaStream_t st) {
+                          int* counters, cudaStream_t st) {
     const int n = hi - lo;
     if (n <= 0) return cudaSuccess;
-    finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctl, inst, lo, hi, fs);
+    finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctl, inst, lo, hi, fs, counters);
     return cudaGetLastError();
 }
 

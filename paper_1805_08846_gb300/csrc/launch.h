@@ -37,9 +37,9 @@ struct FinalSlots {
 
 // Step control (control.cu).
 cudaError_t launch_arm(Control* ctl, int lo, int hi, int mode, long long nsteps, double t_final,
-                       double fixed_dt, double cfl_desired, cudaStream_t st);
+                       double fixed_dt, double cfl_desired, int* counters, cudaStream_t st);
 cudaError_t launch_finish(Control* ctl, const InstDesc* inst, int lo, int hi, FinalSlots fs,
-                          cudaStream_t st);
+                          int* counters, cudaStream_t st);
 cudaError_t launch_speed_reduce(Control* ctl, const InstDesc* inst, int lo, int hi, int set_dt,
                                 cudaStream_t st);
 cudaError_t launch_set_time(Control* ctl, int i, double t, double dt, long long nsteps,

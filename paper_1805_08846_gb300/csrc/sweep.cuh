@@ -208,11 +208,27 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     unsigned char* outbox = smem + STAGES * Cfg::STAGE_BYTES;   // x sweep: result boxes
     uint64_t* bars = reinterpret_cast<uint64_t*>(outbox + Cfg::OUT_BYTES);
 
-    const TileDesc td = A.tiles[blockIdx.x];
-    if (td.inst < A.inst_lo || td.inst >= A.inst_hi) return;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        mbar_init_fence();
+    }
+    // Persistent schedule: each CTA takes the next tile of the (cost-ordered)
+    // list until none is left; the staging ring and its barrier phases run on
+    // across tiles (kbase = chunks this CTA has consumed so far).
+    __shared__ int s_next;
+    int kbase = 0;
+    for (int iter = 0;; ++iter) {
+    if (threadIdx.x == 0)
+        s_next = A.persistent ? atomicAdd(A.tile_counter, 1) : (iter == 0 ? (int)blockIdx.x : A.ntiles);
+    __syncthreads();
+    const int tnext = s_next;
+    __syncthreads();
+    if (tnext >= A.ntiles) break;
+    const TileDesc td = A.tiles[A.order ? A.order[tnext] : tnext];
+    if (td.inst < A.inst_lo || td.inst >= A.inst_hi) continue;
     const InstDesc& I = A.inst[td.inst];
     Control* ctl = A.ctl + td.inst;
-    if (*(volatile int*)&ctl->active == 0) return;
+    if (*(volatile int*)&ctl->active == 0) continue;
 
     const int lane = threadIdx.x;
     long long base, stride;
@@ -245,15 +261,9 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     const CUtensorMap* smap = &A.tma[td.inst].map[DIR];
     const CUtensorMap* amap = &A.tma[td.inst].map[3 + DIR];
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-
-    // Thread 0 issues chunk k into stage k % STAGES.
+    // Thread 0 issues chunk k into stage (kbase + k) % STAGES.
     auto issue = [&](int k) {
-        const int s = k % STAGES;
+        const int s = (kbase + k) % STAGES;
         const uint32_t bar = smem_addr(&bars[s]);
         mbar_arrive_expect_tx(bar, Cfg::STAGE_BYTES);
         const int pos = a + k * C;
@@ -429,8 +439,8 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     int kfail = nchunks;
     int stored = 0;        // x sweep: result boxes already written back
     for (int k = 0; k < nchunks; ++k) {
-        const int s = k % STAGES;
-        const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / STAGES) & 1));
+        const int s = (kbase + k) % STAGES;
+        const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((kbase + k) / STAGES) & 1));
         const unsigned char* stage = smem + s * Cfg::STAGE_BYTES;
         const int jlo = k == 0 ? 2 : 0;                // cells a, a+1 came directly
         const int jhi = min(C, b - (a + k * C));       // cells from b on come directly
@@ -519,7 +529,8 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             atomicOr(&ctl->status, kStatTimeout);
             // chunks kfail .. kfail + STAGES - 1 were issued and not consumed
             for (int k = kfail; k < kfail + STAGES && k < nchunks; ++k)
-                mbar_wait_bounded(smem_addr(&bars[k % STAGES]), (uint32_t)((k / STAGES) & 1));
+                mbar_wait_bounded(smem_addr(&bars[(kbase + k) % STAGES]),
+                                  (uint32_t)(((kbase + k) / STAGES) & 1));
             if (DIR == 0) bulk_wait_all();
         }
         return;
@@ -535,15 +546,19 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         step(c1, false, true, (long long)(b - 1) * stride);
     }
     if (DIR == 0) {
-        // the remaining result boxes (a tail past b is the grid edge: clipped)
+        // the remaining result boxes (a tail past b is the grid edge: clipped);
+        // the next tile refills the boxes, so their reads must be done
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int ko = stored; ko < nchunks; ++ko) store_out(ko);
-            bulk_wait_all();
+            bulk_wait_read<0>();
         }
     }
     reduce_to_control<DIR>(ctl, smax, bad);
+    kbase += nchunks;
+    }  // tile loop
+    if (DIR == 0 && threadIdx.x == 0) bulk_wait_all();
 }
 
 }  // namespace claw

@@ -10,14 +10,22 @@ template <class Sys, class Real, int LIM, int DIR>
 cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     if (L.grid == 0) return cudaSuccess;
     using Cfg = StageCfg<Sys, Real, DIR>;
-    static bool smem_set = false;   // idempotent, so a racing second set is harmless
-    if (!smem_set) {
-        const cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    static int resident = 0;   // CTAs of this kernel the whole GPU holds at once
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        smem_set = true;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR>, kLines,
+                                                          Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        resident = per_sm * sms > 0 ? per_sm * sms : 1;
     }
-    sweep_kernel<Sys, Real, LIM, DIR><<<L.grid, kLines, Cfg::SMEM, L.stream>>>(L.args, P);
+    unsigned grid = L.grid;
+    if (L.args.persistent && grid > (unsigned)resident) grid = (unsigned)resident;
+    sweep_kernel<Sys, Real, LIM, DIR><<<grid, kLines, Cfg::SMEM, L.stream>>>(L.args, P);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,9 @@ class Solver:
     def set_segment(self, d, seg_len):
         L.claw_set_segment(self.h, d, seg_len)
 
+    def autotune(self, trial_steps=3):
+        return L.claw_autotune(self.h, trial_steps)
+
 
 class Ensemble:
     """B independent grids of one system advanced by shared launches."""
@@ -161,3 +164,6 @@ class Ensemble:
 
     def set_segment(self, d, seg_len):
         L.claw_set_segment(self.h, d, seg_len)
+
+    def autotune(self, trial_steps=3):
+        return L.claw_autotune(self.h, trial_steps)

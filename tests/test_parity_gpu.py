@@ -99,6 +99,26 @@ def test_segment_lengths_do_not_change_the_result(seg):
     assert fieldwise_linf(q, ref["q"]) <= TOL64
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_autotune_keeps_state_and_clock(precision):
+    """The segment autotuner runs trial steps but restores state and clock."""
+    prob = inputs.random_problem("shallow_water", (300, 130), "minmod", "extrap", discontinuous=True)
+    ref = Oracle(prob).run_steps(prob.q0, 5)
+    with Solver.from_problem(prob, precision) as s:
+        before = s.time()
+        q_before = s.get_q()
+        seg = s.autotune(2)
+        assert s.time() == before
+        np.testing.assert_array_equal(s.get_q(), q_before)
+        assert all(v >= 4 for v in seg[:2]) and seg[0] % 8 == 0
+        s.run_steps(5)
+        q = s.get_q()
+    if precision == 64:
+        assert fieldwise_linf(q, ref["q"]) <= TOL64
+    else:
+        check_fp32(prob, q, ref["q"])
+
+
 def test_initial_dt_from_speed_pass():
     prob = inputs.sw_radial_dam_break(96)
     M = Oracle(prob).max_speed_over_dx(prob.q0)
