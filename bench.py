@@ -126,6 +126,62 @@ def cpu_oracle_rate(prob, seconds_budget=20.0, max_steps=50):
     return prob.ncells * steps / el, steps, oracle.threads(), el
 
 
+def extra_acoustics3d(args, peak_gbs):
+    """3D variable-coefficient acoustics, two layers, 512^3, walls, MC: FP32
+    and FP64 cell-updates/s, per-sweep times and the HBM fraction of the
+    dominant FP32 sweep (6 values of 4 B per cell and sweep: p, u_d read and
+    written, Z, c read)."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    prob = inputs.acoustics_3d_layers(args.n3)
+    out = {"workload": f"3D two-layer acoustics {args.n3}^3, MC, walls, CFL 0.9"}
+    for prec, steps in ((32, args.steps3), (64, max(2, args.steps3 // 10))):
+        s = Solver.from_problem(prob, precision=prec)
+        seg = s.autotune(2)
+        s.run_steps(3)
+        ms, tot, nl = s.profile_steps(steps)
+        s.close()
+        r = {"value": prob.ncells * steps / (tot * 1e-3), "ms_per_step": tot / steps,
+             "sweep_ms": ms[:3], "steps": steps, "segments": seg}
+        if prec == 32:
+            dom = int(np.argmax(ms[:3]))
+            ach = 24 * prob.ncells / (ms[dom] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+                             "frac": ach / peak_gbs, "kernel": f"sweep dir={'xyz'[dom]}"}
+        out[f"f{prec}"] = r
+    return out
+
+
+def extra_ensembles(args):
+    """Batched FP32 ensembles (one launch per sweep for all instances) against
+    the plain FP64 path run instance by instance on the same instances."""
+    from paper_1805_08846_gb300 import Ensemble, Solver, inputs
+    res = {}
+    for name, gen, steps32, steps64 in (
+            ("sw_256", lambda: inputs.sw_ensemble(), 50, 5),
+            ("acoustics3d_64", lambda: inputs.acoustics3d_ensemble(), 100, 3)):
+        probs = gen()
+        cells = sum(p.ncells for p in probs)
+        e = Ensemble.from_problems(probs, precision=32)
+        seg = e.autotune(1)
+        e.run_steps(3)
+        ms, tot, nl = e.profile_steps(steps32)
+        e.close()
+        v32 = cells * steps32 / (tot * 1e-3)
+        t64 = 0.0
+        for p in probs:
+            s = Solver.from_problem(p, precision=64)
+            s.run_steps(1)
+            ms64, tot64, _ = s.profile_steps(steps64)
+            s.close()
+            t64 += tot64
+        v64 = cells * steps64 / (t64 * 1e-3)
+        res[name] = {"instances": len(probs), "cells": cells, "fp32_batched": v32,
+                     "fp32_steps": steps32, "fp64_per_instance": v64, "fp64_steps": steps64,
+                     "ratio": v32 / v64, "segments": seg, "unit": METRIC}
+        del probs
+    return res
+
+
 def reference_arm(args):
     """The oracle as the reference arm: each step is the full step of the
     workload on a bounded subset of its lines (the x sweep on the first L rows
@@ -184,6 +240,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 3D acoustics and ensemble measurements")
+    ap.add_argument("--n3", type=int, default=512)
+    ap.add_argument("--steps3", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -258,6 +318,15 @@ def main():
                 "ms_per_step": tot64 / args.steps,
                 "sweep_ms": {"x": ms64[0], "y": ms64[1]}}
 
+    extras = {}
+    if not args.no_extras:
+        for key, fn in (("acoustics3d", lambda: extra_acoustics3d(args, peak_gbs)),
+                        ("ensembles", lambda: extra_ensembles(args))):
+            try:
+                extras[key] = fn()
+            except Exception as exc:    # recorded, the main line still prints
+                extras[key] = {"error": repr(exc)[:300]}
+
     if rank != 0:
         return 0
     line = {
@@ -282,6 +351,7 @@ def main():
         "clocks": clk,
         "fp64_plain": fp64,
     }
+    line.update(extras)
     if not args.no_cpu:
         rate, steps, threads, el = cpu_oracle_rate(prob)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",

@@ -1,0 +1,161 @@
+"""Parity at the full sizes of the five benchmark problems, through the C ABI,
+in the launch configuration the benchmark times (persistent sweeps, CUDA
+graphs, autotuned segments).
+
+Where the oracle can run the whole problem on the host cores it does (the
+2D dam break for its stated 200 steps); elsewhere it runs the first steps on
+the full grid, and the stated step counts are checked through properties
+that hold at any size (symmetry, mass conservation) and against the FP64 GPU
+path pinned to the oracle above.  Ensembles are compared instance by
+instance on a seeded sample spanning the size range.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle
+from paper_1805_08846_gb300 import Ensemble, Solver, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def fieldwise_linf(a, b):
+    return max(oracle.rel_linf(a[f], b[f]) for f in range(a.shape[0]))
+
+
+def gpu_run(prob, nsteps, precision, autotune=True):
+    with Solver.from_problem(prob, precision=precision) as s:
+        if autotune:
+            s.autotune(2)
+        s.run_steps(nsteps)
+        q = s.get_q()
+        t = s.time()
+    return q, t
+
+
+@pytest.fixture(scope="module")
+def dam_break():
+    return inputs.sw_radial_dam_break(4096)
+
+
+@pytest.fixture(scope="module")
+def dam_break_oracle_200(dam_break):
+    return Oracle(dam_break).run_steps(dam_break.q0, 200)
+
+
+def test_dam_break_4096_fp64_200_steps(dam_break, dam_break_oracle_200):
+    ref = dam_break_oracle_200
+    q, (t, dt, n) = gpu_run(dam_break, 200, 64)
+    assert n == 200
+    assert t == pytest.approx(ref["t"], rel=1e-13)
+    assert fieldwise_linf(q, ref["q"]) <= TOL64
+
+
+def test_dam_break_4096_fp32_200_steps(dam_break, dam_break_oracle_200):
+    ref = dam_break_oracle_200
+    q, (t, dt, n) = gpu_run(dam_break, 200, 32)
+    err = oracle.rel_l1(q[0], ref["q"][0])
+    assert err <= 1e-4, err
+    # the informative norm: the perturbation h - 1
+    err_pert = oracle.rel_l1(q[0] - 1.0, ref["q"][0] - 1.0)
+    assert err_pert <= 1e-3, err_pert
+    assert t == pytest.approx(ref["t"], rel=1e-5)
+
+
+def test_dam_break_4096_properties_fp32(dam_break):
+    """Mass is conserved (the fronts stay inside [-1,1]^2 over 200 steps)
+    and the x -> -x mirror symmetry holds."""
+    q, _ = gpu_run(dam_break, 200, 32)
+    m0 = math.fsum(dam_break.q0[0].astype(np.float32).astype(np.float64).ravel())
+    assert abs(math.fsum(q[0].ravel()) - m0) <= 2e-6 * m0
+    assert np.abs(q[0] - q[0][:, ::-1]).max() <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def layers():
+    return inputs.acoustics_3d_layers(512)
+
+
+@pytest.fixture(scope="module")
+def layers_oracle_2(layers):
+    return Oracle(layers).run_steps(layers.q0, 2)
+
+
+def test_layers_512_fp64_first_steps(layers, layers_oracle_2):
+    q, (t, dt, n) = gpu_run(layers, 2, 64, autotune=False)
+    assert fieldwise_linf(q, layers_oracle_2["q"]) <= TOL64
+    assert t == pytest.approx(layers_oracle_2["t"], rel=1e-14)
+
+
+def test_layers_512_fp32_first_steps(layers, layers_oracle_2):
+    q, _ = gpu_run(layers, 2, 32, autotune=False)
+    ref = layers_oracle_2["q"]
+    err = max(oracle.rel_l2(q[f], ref[f]) for f in range(4) if np.abs(ref[f]).max() > 0)
+    assert err <= 1e-5, err
+
+
+def test_layers_512_100_steps_fp32_vs_fp64_and_symmetry(layers):
+    """100 steps: the FP32 form against the FP64 path (itself pinned to the
+    oracle), and the pulse's mirror symmetry in x and y."""
+    q64, _ = gpu_run(layers, 100, 64)
+    q32, _ = gpu_run(layers, 100, 32)
+    err = max(oracle.rel_l2(q32[f], q64[f]) for f in range(4))
+    assert err <= 1e-5, err
+    p = q64[0]
+    scale = np.abs(p).max()
+    assert np.abs(p - p[:, :, ::-1]).max() <= 1e-12 * scale
+    assert np.abs(p - p[:, ::-1, :]).max() <= 1e-12 * scale
+    assert np.abs(q64[1] + q64[1][:, :, ::-1]).max() <= 1e-12 * scale
+
+
+SW_SAMPLE = [0, 1, 2, 3, 64, 128, 200, 255]
+
+
+@pytest.fixture(scope="module")
+def sw_ensemble():
+    return inputs.sw_ensemble()
+
+
+def test_sw_ensemble_256_sample_vs_oracle(sw_ensemble):
+    probs = sw_ensemble
+    sizes = [p.n[0] for p in probs]
+    sample = sorted(set(SW_SAMPLE + [int(np.argmin(sizes)), int(np.argmax(sizes))]))
+    for prec in (32, 64):
+        e = Ensemble.from_problems(probs, precision=prec)
+        e.autotune(1)
+        e.run_steps(50)
+        for i in sample:
+            ref = Oracle(probs[i]).run_steps(probs[i].q0, 50)
+            q = e.get_q(i)
+            t, dt, n = e.time(i)
+            assert n == 50
+            if prec == 64:
+                assert fieldwise_linf(q, ref["q"]) <= TOL64, i
+                assert t == pytest.approx(ref["t"], rel=1e-13)
+            else:
+                assert oracle.rel_l1(q[0], ref["q"][0]) <= 1e-4, i
+        e.close()
+
+
+def test_ac3_ensemble_64_vs_fp64_per_instance_and_oracle():
+    probs = inputs.acoustics3d_ensemble()
+    e = Ensemble.from_problems(probs, precision=32)
+    e.autotune(1)
+    e.run_steps(100)
+    sizes = [p.n[0] for p in probs]
+    smallest = list(np.argsort(sizes)[:2])
+    for i, p in enumerate(probs):
+        q32 = e.get_q(i)
+        with Solver.from_problem(p, precision=64) as s:
+            s.run_steps(100)
+            q64 = s.get_q()
+        err = max(oracle.rel_l2(q32[f], q64[f]) for f in range(4))
+        assert err <= 1e-5, (i, err)
+        if i in smallest:
+            ref = Oracle(p).run_steps(p.q0, 100)
+            assert fieldwise_linf(q64, ref["q"]) <= TOL64, i
+    e.close()
