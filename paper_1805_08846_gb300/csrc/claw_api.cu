@@ -424,7 +424,11 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
             I.n[d] = d < ndim ? grids[i].n[d] : 1;
             I.dx[d] = d < ndim ? grids[i].dx[d] : 1.0;
         }
+        // Row pitch: a multiple of 32 elements (128 B FP32 rows), made an odd
+        // multiple so that the rows an x-sweep box spans do not all start at
+        // the same power-of-two stride (they would crowd a few HBM channels).
         I.pitch = (I.n[0] + 31) / 32 * 32;
+        if ((I.pitch / 32) % 2 == 0) I.pitch += 32;
         I.fstride = (long long)I.n[2] * I.n[1] * I.pitch;
         I.vstride = (long long)m * I.fstride;
         I.offset = off;
@@ -723,7 +727,8 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
     if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
     if (seg_len < 4) return fail(CLAW_EINVAL, "segment length must be >= 4");
     CK(cudaStreamSynchronize(s->stream));
-    // x segments start on 32-byte boundaries (the bulk copies' alignment rule)
+    // x segments are whole x chunks (32 bytes: 8 FP32 / 4 FP64 cells), which
+    // also keeps their starts on the bulk copies' 16-byte boundary
     s->seg[d] = d == 0 ? (seg_len + 7) / 8 * 8 : seg_len;
     return build_tiles(s);
 }

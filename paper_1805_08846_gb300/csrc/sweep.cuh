@@ -23,10 +23,11 @@
 // memory buffers, several chunks ahead of the march, so the HBM stream is
 // deep enough without any per-thread prefetch registers.  For the y and z
 // sweeps a chunk is C rows of kLines consecutive x (one 512 B row per field
-// for FP32); for the x sweep it is kLines rows of C consecutive x, stored
-// with the 32-byte swizzle so that each thread's two 16-byte reads of its own
-// row are free of bank conflicts.  The two cells before and after the
-// segment (ghosts at the domain edge) are read directly.
+// for FP32) and results are stored directly (a warp writes 32 consecutive x).
+// For the x sweep a chunk is 32 bytes of each of kLines rows (32-byte
+// swizzle, conflict-free 16-byte reads), and each row's results are gathered
+// into 16-byte words in registers and written as whole words.  The two cells
+// before and after the segment (ghosts at the domain edge) are read directly.
 #pragma once
 #include "claw_types.cuh"
 #include "riemann.cuh"
@@ -171,20 +172,20 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
 // ------------------------------------------------------------------------
 // The staged sweep.
 // ------------------------------------------------------------------------
-// Every plane box is 4 KB: 32 bytes of each of the 128 lines (x sweep) or
-// 4 KB / (128 * sizeof(Real)) cells of 128 adjacent lines (y, z sweeps).
-// The x sweep also stages its results: OUTBUF boxes per touched field, each
-// written back by one bulk-tensor store once its C cells are final.
+// A plane box holds 32 bytes' worth of cells (8 FP32 / 4 FP64) of 128
+// lines, 4 KB: for the y, z sweeps C rows of 128 adjacent x, for the x sweep
+// 32 bytes of each of 128 rows, kept with the 32-byte swizzle (the two
+// 16-byte halves of a row swap places on bit 2 of the row) so that a warp's
+// 16-byte reads of its own rows hit every bank once.
 template <class Sys, class Real, int DIR>
 struct StageCfg {
     static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
+    static constexpr int G = 16 / (int)sizeof(Real);            // cells per 16-byte half
     static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
-    static constexpr int STAGES = DIR == 0 ? 3 : 4;
+    static constexpr int STAGES = 4;
     static constexpr int STAGE_BYTES = NP * BOX;
-    static constexpr int OUTBUF = DIR == 0 ? 3 : 0;
-    static constexpr int OUT_BYTES = OUTBUF * Sys::NQ * BOX;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + OUT_BYTES + 1024 + 64;  // + alignment, barriers
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
     static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;   // register budget per thread
 };
 
@@ -205,8 +206,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* outbox = smem + STAGES * Cfg::STAGE_BYTES;   // x sweep: result boxes
-    uint64_t* bars = reinterpret_cast<uint64_t*>(outbox + Cfg::OUT_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
@@ -343,10 +343,10 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             for (int c = 0; c < NQ; ++c) F[c] += k * wB.W[p][c];
         }
     };
-    // Consume cell I+1: solve interface I+1, limit interface I, update cell
-    // I-1 (out of place).  SPEED: interface I+1 bounds an interior cell of
+    // Consume cell I+1: solve interface I+1, limit interface I, form the new
+    // state qn of cell I-1.  SPEED: interface I+1 bounds an interior cell of
     // the segment.  UPDATE: cell I-1 belongs to the segment.
-    auto step = [&](const Cell& cur, bool speed, bool update, long long cell_off) {
+    auto step = [&](const Cell& cur, bool speed, bool update, Real* qn) {
         W wC;
         Sys::solve(prev, cur, P, wC);
         if (valid && speed) smax = max(smax, speed_bits(Sys::max_speed(wC)));
@@ -359,30 +359,13 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         Real F1[NQ];
         flux(dAB, dBC, F1);
         if (update) {
-            Real qn[NQ];
 #pragma unroll
             for (int c = 0; c < NQ; ++c) {
                 const Real first = apdqA[c] + wB.amdq[c];
                 const Real second = F1[c] - F0[c];
                 qn[c] = qkeep[c] - nu * first - nu * second;
             }
-            if (DIR == 0) {
-                // cell_off is the cell index along x: its column in result box
-                // (cell - a) / C, with the same 32-byte swizzle as the inputs
-                const int rel = (int)cell_off - a;
-                unsigned char* box = outbox + ((rel / C) % Cfg::OUTBUF) * (NQ * Cfg::BOX);
-                const int col = rel % C;
-                const int byte = ((((col * (int)sizeof(Real)) >> 4) ^ ((lane >> 2) & 1)) << 4) +
-                                 ((col * (int)sizeof(Real)) & 15);
-#pragma unroll
-                for (int c = 0; c < NQ; ++c)
-                    *reinterpret_cast<Real*>(box + c * Cfg::BOX + lane * 32 + byte) = qn[c];
-                if (valid) bad |= Sys::nonphysical(qn);
-            } else if (valid) {
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) qout[c][cell_off] = qn[c];
-                bad |= Sys::nonphysical(qn);
-            }
+            if (valid) bad |= Sys::nonphysical(qn);
         }
 #pragma unroll
         for (int c = 0; c < NQ; ++c) {
@@ -423,21 +406,45 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         }
         prev = c0;                                     // cell a
         load_direct(a + 1, c1);
-        step(c1, true, false, 0);            // interface a+1, flux at a
+        Real unused[NQ];
+        step(c1, true, false, unused);                // interface a+1, flux at a
     }
 
-    // x sweep: bulk-store result box of output chunk ko (cells a+ko*C ..).
-    auto store_out = [&](int ko) {
-        const unsigned char* box = outbox + (ko % Cfg::OUTBUF) * (NQ * Cfg::BOX);
+    // New state of cell i straight to global memory (y, z: a warp writes 32
+    // consecutive x).  The x sweep gathers each row's results into 16-byte
+    // words in registers and writes whole words (4 FP32 / 2 FP64 cells).
+    auto put_global = [&](int i, const Real* qn) {
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) qout[c][(long long)i * stride] = qn[c];
+        }
+    };
+    constexpr int G = Cfg::G;
+    const int sw = (lane >> 2) & 1;    // 32-byte swizzle of row `lane`
+    Real ob[NQ][G];        // x sweep: the 16-byte result word being assembled
+
+    // x sweep: results go back into the input stage they came from (each
+    // result overwrites an input position already consumed) and leave by
+    // bulk-tensor stores, so the staging buffers are shared by both ways.
+    auto stage_of = [&](int kk) { return smem + ((kbase + kk) % STAGES) * Cfg::STAGE_BYTES; };
+    auto put_stage_scalar = [&](int i, const Real* qn) {
+        const int rel = i - a;
+        unsigned char* st = stage_of(rel / C);
+        const int byte = lane * 32 + 16 * (((rel % C) / G) ^ sw) + (rel % G) * (int)sizeof(Real);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(st + c * Cfg::BOX + byte) = qn[c];
+    };
+    auto store_stage = [&](int kk) {       // thread 0
+        const unsigned char* st = stage_of(kk);
 #pragma unroll
         for (int c = 0; c < NQ; ++c)
-            tma_store_3d(smap, smem_addr(box + c * Cfg::BOX), a + ko * C, td.line0, plane_out[c]);
+            tma_store_3d(smap, smem_addr(st + c * Cfg::BOX), a + kk * C, td.line0, plane_out[c]);
         bulk_commit();
     };
+    int stored = 0;        // x sweep: output chunks already written back
 
     bool ok = true;
     int kfail = nchunks;
-    int stored = 0;        // x sweep: result boxes already written back
     for (int k = 0; k < nchunks; ++k) {
         const int s = (kbase + k) % STAGES;
         const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((kbase + k) / STAGES) & 1));
@@ -446,9 +453,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         const int jhi = min(C, b - (a + k * C));       // cells from b on come directly
         // Cells come straight from shared memory as they are marched over;
         // the stage is released once the whole chunk has been consumed.
-        auto consume = [&](int j, const Real* vals) {
-            const int Iif = a + k * C + j;
-            Cell cur;
+        auto make_cell = [&](const Real* vals, Cell& cur) {
 #pragma unroll
             for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
             if constexpr (NA > 0) {
@@ -456,15 +461,12 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
                 cur.c = vals[NQ + 1];
             }
             Sys::prepare(cur, P);
-            step(cur, true, true, (long long)(Iif - 2) * stride);
         };
         if (DIR == 0) {
-            // row = lane, 32 bytes; the 16-byte halves are swapped on bit 2 of the row
-            constexpr int H = 16 / (int)sizeof(Real);     // cells per half row
-            const int sw = (lane >> 2) & 1;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                Real hv[NP][H];
+                // 16-byte half h of row `lane` (G cells) per plane
+                Real hv[NP][G];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                     const unsigned char* row = stage + p * Cfg::BOX + lane * 32 + 16 * (h ^ sw);
@@ -477,13 +479,51 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < H; ++j) {
-                    const int jj = h * H + j;
-                    if (jj >= jlo && jj < jhi) {
+                for (int jj = 0; jj < G; ++jj) {
+                    const int j = h * G + jj;
+                    if (j >= jlo && j < jhi) {
                         Real vals[NP];
 #pragma unroll
-                        for (int p = 0; p < NP; ++p) vals[p] = hv[p][j];
-                        consume(jj, vals);
+                        for (int p = 0; p < NP; ++p) vals[p] = hv[p][jj];
+                        Cell cur;
+                        make_cell(vals, cur);
+                        Real qn[NQ];
+                        step(cur, true, true, qn);
+                        // new state of output cell rel = k*C + j - 2; its place
+                        // in a 16-byte half is (j - 2) mod G
+                        const int pos = (j + C - 2) % G;
+#pragma unroll
+                        for (int c = 0; c < NQ; ++c) ob[c][pos] = qn[c];
+                        if (pos == G - 1) {
+                            // half complete: output chunk k-1 half 1 (j = 1) or
+                            // output chunk k half 0 (j = G + 1)
+                            unsigned char* st = stage_of(j < 2 ? k - 1 : k);
+                            const int half = j < 2 ? 1 : 0;
+#pragma unroll
+                            for (int c = 0; c < NQ; ++c) {
+                                unsigned char* dst = st + c * Cfg::BOX + lane * 32 + 16 * (half ^ sw);
+                                if constexpr (sizeof(Real) == 4)
+                                    *reinterpret_cast<float4*>(dst) =
+                                        make_float4(ob[c][0], ob[c][1], ob[c][2], ob[c][3]);
+                                else
+                                    *reinterpret_cast<double2*>(dst) = make_double2(ob[c][0], ob[c][1]);
+                            }
+                        }
+                        if (j == 1) {
+                            // output chunk k-1 is complete in its stage: write it
+                            // back; the write-back issued one chunk ago has had
+                            // time to read its stage, which is refilled now
+                            fence_proxy_async_smem();
+                            __syncthreads();
+                            if (threadIdx.x == 0) {
+                                store_stage(k - 1);
+                                if (k >= 2) {
+                                    bulk_wait_read<1>();
+                                    if (k - 2 + STAGES < nchunks) issue(k - 2 + STAGES);
+                                }
+                            }
+                            stored = k;
+                        }
                     }
                 }
             }
@@ -494,15 +534,12 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
 #pragma unroll
                 for (int p = 0; p < NP; ++p)
                     vals[p] = reinterpret_cast<const Real*>(stage + p * Cfg::BOX)[j * kLines + lane];
-                consume(j, vals);
+                Cell cur;
+                make_cell(vals, cur);
+                Real qn[NQ];
+                step(cur, true, true, qn);
+                put_global(a + k * C + j - 2, qn);
             }
-        }
-        if (DIR == 0) {
-            // result writes -> async proxy; the store that last used the box the
-            // next chunk starts filling (OUTBUF = 3: issued one chunk ago) must
-            // have finished reading it
-            fence_proxy_async_smem();
-            if (threadIdx.x == 0) bulk_wait_read<0>();
         }
         // Every thread is done with stage s: it may be refilled.  The vote
         // makes a timed-out wait a uniform decision of the CTA (the chunk's
@@ -512,14 +549,8 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             kfail = k;
             break;
         }
-        // Result box k-1 got its last two cells from cells j = 0, 1 of this
-        // chunk -- unless the chunk holds fewer than two cells, in which case
-        // they come from the epilogue and the box is written back after it.
-        if (DIR == 0 && k >= 1 && b - (a + k * C) >= 2) {
-            if (threadIdx.x == 0) store_out(k - 1);
-            stored = k;
-        }
-        if (threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
+        // y, z: stage s is consumed, refill it (x refills after its write-back)
+        if (DIR != 0 && threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
     }
 
     if (!ok) {
@@ -536,22 +567,43 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         return;
     }
 
+    if (DIR == 0) {
+        // Result cells still in registers: the stream produced output cells
+        // rel = 0 .. b - a - 3, and every completed 16-byte half was written
+        // as it completed.
+        const int r1 = b - a - 2;
+        const int r0 = r1 > 0 ? (r1 / G) * G : 0;
+#pragma unroll
+        for (int pos = 0; pos < G; ++pos) {
+            if (r0 + pos < r1) {
+                Real qn[NQ];
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) qn[c] = ob[c][pos];
+                put_stage_scalar(a + r0 + pos, qn);
+            }
+        }
+    }
+
     // Epilogue (direct loads): cells b, b+1; the last interface b+1 bounds no
     // interior cell of the segment.
     {
         Cell c1;
+        Real qn[NQ];
         load_direct(b, c1);
-        step(c1, true, true, (long long)(b - 2) * stride);
+        step(c1, true, true, qn);
+        if (DIR == 0) put_stage_scalar(b - 2, qn); else put_global(b - 2, qn);
         load_direct(b + 1, c1);
-        step(c1, false, true, (long long)(b - 1) * stride);
+        step(c1, false, true, qn);
+        if (DIR == 0) put_stage_scalar(b - 1, qn); else put_global(b - 1, qn);
     }
     if (DIR == 0) {
-        // the remaining result boxes (a tail past b is the grid edge: clipped);
-        // the next tile refills the boxes, so their reads must be done
+        // write back the output chunks still in their stages (a tail past b
+        // is the grid edge: clipped); the next tile refills the stages, so the
+        // reads must be done
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int ko = stored; ko < nchunks; ++ko) store_out(ko);
+            for (int ko = stored; ko < nchunks; ++ko) store_stage(ko);
             bulk_wait_read<0>();
         }
     }
