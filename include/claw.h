@@ -216,8 +216,8 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
                                double* total_ms, long* launches);
 
 /* Tuning knobs (the autotuner drives these): cells per line segment of one
- * thread in direction d (>= 4; x segments are rounded up to a multiple of 8).
- * Rebuilds the tile lists. */
+ * thread in direction d (>= 4, rounded up to a multiple of 8).  Rebuilds the
+ * tile lists. */
 claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 
 /* Autotuner: for every direction, time trial_steps steps (CUDA events around

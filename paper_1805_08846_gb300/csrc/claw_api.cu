@@ -120,8 +120,9 @@ claw_status build_tiles(claw_solver* s) {
             const InstDesc& I = s->inst[i];
             const int lo = (int)T.size();
             const int N = I.n[d];
-            // Segments [a, b) of length L; a tail shorter than 2 cells joins
-            // the segment before it (the sweep kernel needs b - a >= 2).
+            // Segments [a, b) of length L (a multiple of 8); a tail shorter
+            // than 2 cells joins the segment before it (the sweep kernel needs
+            // b - a >= 2); only the last segment of a line ends mid-chunk.
             std::vector<std::pair<int, int>> segs;
             for (int a = 0; a < N; a += L) segs.push_back({a, std::min(a + L, N)});
             if (segs.size() > 1 && segs.back().second - segs.back().first < 2) {
@@ -311,12 +312,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 claw_status encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
-                   const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swz) {
+                   const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swz,
+                   CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B) {
     auto fn = encode_fn();
     if (!fn) return fail(CLAW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUresult r = fn(map, dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(CLAW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return CLAW_OK;
 }
@@ -727,9 +729,11 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
     if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
     if (seg_len < 4) return fail(CLAW_EINVAL, "segment length must be >= 4");
     CK(cudaStreamSynchronize(s->stream));
-    // x segments are whole x chunks (32 bytes: 8 FP32 / 4 FP64 cells), which
-    // also keeps their starts on the bulk copies' 16-byte boundary
-    s->seg[d] = d == 0 ? (seg_len + 7) / 8 * 8 : seg_len;
+    // Segments are whole chunks (8 cells: 32 bytes of FP32, 2 chunks of
+    // FP64): a chunk's results leave as one bulk store, so a segment may end
+    // mid-chunk only at the grid edge, where the store is clipped.  For the
+    // x sweep this also keeps chunk starts on the bulk copies' 16-byte boundary.
+    s->seg[d] = (seg_len + 7) / 8 * 8;
     return build_tiles(s);
 }
 

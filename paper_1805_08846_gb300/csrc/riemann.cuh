@@ -126,6 +126,7 @@ struct Acoustics {
     __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
         return !(fabs(q[0]) <= (Real)3.0e38);
     }
+    static constexpr bool kMinH = false;
 };
 
 // ------------------------------------------------------------------------
@@ -272,6 +273,10 @@ struct ShallowWater {
     __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
         return !(q[0] > Real(0) && q[0] <= (Real)3.0e38);
     }
+    // Cheaper form for the sweep: fold h's bit pattern into a running
+    // signed-integer minimum; a minimum <= 0 means some h <= 0 (a NaN h
+    // makes the next sweep's speeds NaN, caught there).
+    static constexpr bool kMinH = true;
 };
 
 // ------------------------------------------------------------------------
@@ -287,6 +292,22 @@ __device__ __forceinline__ Real limiter_phi(Real theta) {
     if (LIM == kLimMC)
         return fmax(Real(0), fmin(fmin(Real(0.5) * (Real(1) + theta), Real(2)), Real(2) * theta));
     return Real(1);
+}
+
+// phi(num / den) for den >= 0.  FP32: a saturating multiply by the SFU
+// reciprocal -- minmod is sat(theta); MC is 2 sat(min(theta, (1 + theta)/4)),
+// the same function written around the clamp to [0, 1] (a NaN ratio of a
+// zero wave saturates to 0).  FP64: the correctly rounded ratio.
+template <int LIM, class Real>
+__device__ __forceinline__ Real limiter_ratio(Real num, Real den) {
+    if constexpr (sizeof(Real) == 4) {
+        const float theta = num * __fdividef(1.0f, den);
+        if (LIM == kLimMinmod) return __saturatef(theta);
+        if (LIM == kLimMC) return 2.0f * __saturatef(fminf(theta, 0.25f + 0.25f * theta));
+        return 1.0f;
+    } else {
+        return limiter_phi<LIM, Real>(num / den);
+    }
 }
 
 }  // namespace claw

@@ -183,10 +183,15 @@ struct StageCfg {
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
     static constexpr int G = 16 / (int)sizeof(Real);            // cells per 16-byte half
     static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = 3;
+    // x sweep results leave through their input stages and bulk stores
+    // (measured: direct stores from 32 rows per warp are 3x slower)
+    static constexpr bool XWB = true;
     static constexpr int STAGE_BYTES = NP * BOX;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
-    static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;   // register budget per thread
+    // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
+    // a 5-CTA budget forces worse schedules), 2 for FP64
+    static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;
 };
 
 template <class Sys, class Real, int LIM, int DIR>
@@ -307,6 +312,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     const Real nu = (Real)(ctl->dt_attempt / I.dx[DIR]);
     SM smax = 0;
     bool bad = false;
+    int hbits = 0x7fffffff;   // running minimum of h's (high) bit pattern
 
     // March state after interface I (between cells I-1 and I) is solved:
     //   prev   cell I (with its per-cell precomputation)
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             Real phi = Real(1);
             if (LIM != kLimNone) {
                 const Real num = sp > Real(0) ? d_up_left[p] : d_up_right[p];
-                phi = limiter_phi<LIM, Real>(Ops<Real>::div(num, ssB[p]));
+                phi = limiter_ratio<LIM, Real>(num, ssB[p]);
             }
             const Real as = fabs(sp);
             const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
@@ -365,7 +371,14 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
                 const Real second = F1[c] - F0[c];
                 qn[c] = qkeep[c] - nu * first - nu * second;
             }
-            if (valid) bad |= Sys::nonphysical(qn);
+            if (valid) {
+                if constexpr (Sys::kMinH) {
+                    if constexpr (sizeof(Real) == 4) hbits = min(hbits, __float_as_int(qn[0]));
+                    else hbits = min(hbits, (int)(__double_as_longlong(qn[0]) >> 32));
+                } else {
+                    bad |= Sys::nonphysical(qn);
+                }
+            }
         }
 #pragma unroll
         for (int c = 0; c < NQ; ++c) {
@@ -410,9 +423,8 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         step(c1, true, false, unused);                // interface a+1, flux at a
     }
 
-    // New state of cell i straight to global memory (y, z: a warp writes 32
-    // consecutive x).  The x sweep gathers each row's results into 16-byte
-    // words in registers and writes whole words (4 FP32 / 2 FP64 cells).
+    // y, z sweeps: the new state of cell i goes straight to global memory (a
+    // warp writes 32 consecutive x, whole 128-byte lines).
     auto put_global = [&](int i, const Real* qn) {
         if (valid) {
 #pragma unroll
@@ -421,27 +433,36 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     };
     constexpr int G = Cfg::G;
     const int sw = (lane >> 2) & 1;    // 32-byte swizzle of row `lane`
-    Real ob[NQ][G];        // x sweep: the 16-byte result word being assembled
 
     // x sweep: results go back into the input stage they came from (each
     // result overwrites an input position already consumed) and leave by
-    // bulk-tensor stores, so the staging buffers are shared by both ways.
+    // bulk-tensor stores, so the staging buffers serve both ways (a warp's
+    // direct stores would touch 32 rows).  Byte offset of chunk position jj
+    // of line `lane` inside a plane box:
+    auto pos_off = [&](int jj) {
+        return DIR == 0 ? lane * 32 + 16 * ((jj / G) ^ sw) + (jj % G) * (int)sizeof(Real)
+                        : (jj * kLines + lane) * (int)sizeof(Real);
+    };
     auto stage_of = [&](int kk) { return smem + ((kbase + kk) % STAGES) * Cfg::STAGE_BYTES; };
-    auto put_stage_scalar = [&](int i, const Real* qn) {
+    auto put_stage = [&](int i, const Real* qn) {
         const int rel = i - a;
-        unsigned char* st = stage_of(rel / C);
-        const int byte = lane * 32 + 16 * (((rel % C) / G) ^ sw) + (rel % G) * (int)sizeof(Real);
+        unsigned char* st = stage_of(rel / C) + pos_off(rel % C);
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(st + c * Cfg::BOX + byte) = qn[c];
+        for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(st + c * Cfg::BOX) = qn[c];
     };
     auto store_stage = [&](int kk) {       // thread 0
         const unsigned char* st = stage_of(kk);
+        const int pos = a + kk * C;
 #pragma unroll
-        for (int c = 0; c < NQ; ++c)
-            tma_store_3d(smap, smem_addr(st + c * Cfg::BOX), a + kk * C, td.line0, plane_out[c]);
+        for (int c = 0; c < NQ; ++c) {
+            const uint32_t src = smem_addr(st + c * Cfg::BOX);
+            if (DIR == 0) tma_store_3d(smap, src, pos, td.line0, plane_out[c]);
+            else if (DIR == 1) tma_store_4d(smap, src, td.line0, pos, td.other, plane_out[c]);
+            else tma_store_4d(smap, src, td.line0, td.other, pos, plane_out[c]);
+        }
         bulk_commit();
     };
-    int stored = 0;        // x sweep: output chunks already written back
+    int stored = 0;        // output chunks already written back
 
     bool ok = true;
     int kfail = nchunks;
@@ -462,83 +483,38 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             }
             Sys::prepare(cur, P);
         };
-        if (DIR == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                // 16-byte half h of row `lane` (G cells) per plane
-                Real hv[NP][G];
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const unsigned char* row = stage + p * Cfg::BOX + lane * 32 + 16 * (h ^ sw);
-                    if constexpr (sizeof(Real) == 4) {
-                        const float4 t = *reinterpret_cast<const float4*>(row);
-                        hv[p][0] = t.x; hv[p][1] = t.y; hv[p][2] = t.z; hv[p][3] = t.w;
-                    } else {
-                        const double2 t = *reinterpret_cast<const double2*>(row);
-                        hv[p][0] = t.x; hv[p][1] = t.y;
-                    }
-                }
-#pragma unroll
-                for (int jj = 0; jj < G; ++jj) {
-                    const int j = h * G + jj;
-                    if (j >= jlo && j < jhi) {
-                        Real vals[NP];
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) vals[p] = hv[p][jj];
-                        Cell cur;
-                        make_cell(vals, cur);
-                        Real qn[NQ];
-                        step(cur, true, true, qn);
-                        // new state of output cell rel = k*C + j - 2; its place
-                        // in a 16-byte half is (j - 2) mod G
-                        const int pos = (j + C - 2) % G;
-#pragma unroll
-                        for (int c = 0; c < NQ; ++c) ob[c][pos] = qn[c];
-                        if (pos == G - 1) {
-                            // half complete: output chunk k-1 half 1 (j = 1) or
-                            // output chunk k half 0 (j = G + 1)
-                            unsigned char* st = stage_of(j < 2 ? k - 1 : k);
-                            const int half = j < 2 ? 1 : 0;
-#pragma unroll
-                            for (int c = 0; c < NQ; ++c) {
-                                unsigned char* dst = st + c * Cfg::BOX + lane * 32 + 16 * (half ^ sw);
-                                if constexpr (sizeof(Real) == 4)
-                                    *reinterpret_cast<float4*>(dst) =
-                                        make_float4(ob[c][0], ob[c][1], ob[c][2], ob[c][3]);
-                                else
-                                    *reinterpret_cast<double2*>(dst) = make_double2(ob[c][0], ob[c][1]);
-                            }
-                        }
-                        if (j == 1) {
-                            // output chunk k-1 is complete in its stage: write it
-                            // back; the write-back issued one chunk ago has had
-                            // time to read its stage, which is refilled now
-                            fence_proxy_async_smem();
-                            __syncthreads();
-                            if (threadIdx.x == 0) {
-                                store_stage(k - 1);
-                                if (k >= 2) {
-                                    bulk_wait_read<1>();
-                                    if (k - 2 + STAGES < nchunks) issue(k - 2 + STAGES);
-                                }
-                            }
-                            stored = k;
-                        }
-                    }
-                }
-            }
-        } else {
+        // One cell of line `lane` at a time.  x sweep: the result of cell
+        // a + k*C + j - 2 overwrites an input position of this or the previous
+        // chunk that has already been consumed.
 #pragma unroll 2
-            for (int j = jlo; j < jhi; ++j) {
-                Real vals[NP];
+        for (int j = jlo; j < jhi; ++j) {
+            const int off = pos_off(j);
+            Real vals[NP];
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
-                    vals[p] = reinterpret_cast<const Real*>(stage + p * Cfg::BOX)[j * kLines + lane];
-                Cell cur;
-                make_cell(vals, cur);
-                Real qn[NQ];
-                step(cur, true, true, qn);
+            for (int p = 0; p < NP; ++p) vals[p] = *reinterpret_cast<const Real*>(stage + p * Cfg::BOX + off);
+            Cell cur;
+            make_cell(vals, cur);
+            Real qn[NQ];
+            step(cur, true, true, qn);
+            if (DIR != 0 || !Cfg::XWB) {
                 put_global(a + k * C + j - 2, qn);
+                continue;
+            }
+            put_stage(a + k * C + j - 2, qn);
+            if (j == 1) {
+                // output chunk k-1 is complete in its stage: write it back; the
+                // write-back issued one chunk ago has had time to read its
+                // stage, which is refilled now
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    store_stage(k - 1);
+                    if (k >= 2) {
+                        bulk_wait_read<1>();
+                        if (k - 2 + STAGES < nchunks) issue(k - 2 + STAGES);
+                    }
+                }
+                stored = k;
             }
         }
         // Every thread is done with stage s: it may be refilled.  The vote
@@ -549,8 +525,9 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             kfail = k;
             break;
         }
-        // y, z: stage s is consumed, refill it (x refills after its write-back)
-        if (DIR != 0 && threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
+        // stage s is consumed, refill it (an x sweep writing back through its
+        // stages refills after the write-back)
+        if ((DIR != 0 || !Cfg::XWB) && threadIdx.x == 0 && k + STAGES < nchunks) issue(k + STAGES);
     }
 
     if (!ok) {
@@ -562,26 +539,9 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             for (int k = kfail; k < kfail + STAGES && k < nchunks; ++k)
                 mbar_wait_bounded(smem_addr(&bars[(kbase + k) % STAGES]),
                                   (uint32_t)(((kbase + k) / STAGES) & 1));
-            if (DIR == 0) bulk_wait_all();
+            if (DIR == 0 && Cfg::XWB) bulk_wait_all();
         }
         return;
-    }
-
-    if (DIR == 0) {
-        // Result cells still in registers: the stream produced output cells
-        // rel = 0 .. b - a - 3, and every completed 16-byte half was written
-        // as it completed.
-        const int r1 = b - a - 2;
-        const int r0 = r1 > 0 ? (r1 / G) * G : 0;
-#pragma unroll
-        for (int pos = 0; pos < G; ++pos) {
-            if (r0 + pos < r1) {
-                Real qn[NQ];
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) qn[c] = ob[c][pos];
-                put_stage_scalar(a + r0 + pos, qn);
-            }
-        }
     }
 
     // Epilogue (direct loads): cells b, b+1; the last interface b+1 bounds no
@@ -591,12 +551,12 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         Real qn[NQ];
         load_direct(b, c1);
         step(c1, true, true, qn);
-        if (DIR == 0) put_stage_scalar(b - 2, qn); else put_global(b - 2, qn);
+        if (DIR == 0 && Cfg::XWB) put_stage(b - 2, qn); else put_global(b - 2, qn);
         load_direct(b + 1, c1);
         step(c1, false, true, qn);
-        if (DIR == 0) put_stage_scalar(b - 1, qn); else put_global(b - 1, qn);
+        if (DIR == 0 && Cfg::XWB) put_stage(b - 1, qn); else put_global(b - 1, qn);
     }
-    if (DIR == 0) {
+    if (DIR == 0 && Cfg::XWB) {
         // write back the output chunks still in their stages (a tail past b
         // is the grid edge: clipped); the next tile refills the stages, so the
         // reads must be done
@@ -607,10 +567,10 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
             bulk_wait_read<0>();
         }
     }
-    reduce_to_control<DIR>(ctl, smax, bad);
+    reduce_to_control<DIR>(ctl, smax, bad || hbits <= 0);
     kbase += nchunks;
     }  // tile loop
-    if (DIR == 0 && threadIdx.x == 0) bulk_wait_all();
+    if (DIR == 0 && Cfg::XWB && threadIdx.x == 0) bulk_wait_all();
 }
 
 }  // namespace claw
