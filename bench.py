@@ -28,6 +28,12 @@ sys.path.insert(0, ROOT)
 
 N_DEFAULT = 4096
 METRIC = "cell-updates/s"
+# Algorithmic flops of one shallow-water cell per sweep: the paper's Nsight
+# count of 313 flop per cell-step over its two sweeps (Tables 1-2 give the
+# per-sweep MFlop at 1024^2).  Our FP32 sweep executes 158.7 per cell; the
+# FP64 sweep executes 322 (double divide / square root expand into FMA
+# sequences) -- both counted with ncu, see profiles/.
+SW_FLOP_PER_CELL_SWEEP = 313.0 / 2.0
 
 
 def load_peaks():
@@ -314,9 +320,18 @@ def main():
     fp64 = None
     if not args.no_fp64:
         ms64, tot64, _ = timed(64)
+        fma64 = L.claw_probe_fma(64)
+        dom64 = 0 if ms64[0] >= ms64[1] else 1
+        ach64 = SW_FLOP_PER_CELL_SWEEP * ncell / (ms64[dom64] * 1e-3)
         fp64 = {"value": world * ncell * args.steps / (tot64 * 1e-3), "unit": METRIC,
                 "ms_per_step": tot64 / args.steps,
-                "sweep_ms": {"x": ms64[0], "y": ms64[1]}}
+                "sweep_ms": {"x": ms64[0], "y": ms64[1]},
+                "roofline": {"bound": "alu", "achieved": ach64 / 1e12, "peak": fma64 / 1e12,
+                             "unit": "TFLOP/s", "frac": ach64 / fma64,
+                             "peak_kind": "measured FP64 FMA probe (claw_probe_fma)",
+                             "flop_per_cell_sweep": SW_FLOP_PER_CELL_SWEEP,
+                             "executed_dflop_per_cell_sweep": 322.0,
+                             "executed_frac": 322.0 * ncell / (ms64[dom64] * 1e-3) / fma64}}
 
     extras = {}
     if not args.no_extras:

@@ -215,6 +215,12 @@ claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system system,
 claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
                                double* total_ms, long* launches);
 
+/* Fused multiply-add throughput of this GPU (flop/s, 2 per FMA) in FP32 or
+ * FP64, measured with independent FMA chains on every SM -- the arithmetic
+ * roof the sweeps are compared with (Sec. 7.1 measures the same "achievable
+ * roof").  Synchronises cuda_stream (NULL = legacy default stream). */
+claw_status claw_probe_fma(int precision, double* flops_per_s, void* cuda_stream);
+
 /* Tuning knobs (the autotuner drives these): cells per line segment of one
  * thread in direction d (>= 4, rounded up to a multiple of 8).  Rebuilds the
  * tile lists. */

@@ -69,6 +69,7 @@ _SIGS = {
     "claw_profile_steps": [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_long)],
     "claw_set_segment": [_vp, C.c_int, C.c_int],
     "claw_autotune": [_vp, C.c_int, C.POINTER(C.c_int)],
+    "claw_probe_fma": [C.c_int, _dp, _vp],
     "claw_max_speed_noalloc": [C.POINTER(claw_grid), C.c_int, C.POINTER(C.c_int),
                                C.POINTER(claw_params), _vp, _vp, _vp, _vp, _vp],
 }
@@ -290,6 +291,12 @@ def claw_profile_steps(h, nsteps):
 
 def claw_set_segment(h, d, seg_len):
     _check(lib().claw_set_segment(h, int(d), int(seg_len)), "claw_set_segment")
+
+
+def claw_probe_fma(precision, stream=None):
+    v = C.c_double(0.0)
+    _check(lib().claw_probe_fma(int(precision), C.byref(v), _stream_arg(stream)), "claw_probe_fma")
+    return v.value
 
 
 def claw_autotune(h, trial_steps=3):

@@ -314,3 +314,10 @@ def test_ensemble_instances_keep_their_own_time_steps():
     np.testing.assert_allclose(dts, refs, rtol=1e-14)
     assert len(set(dts)) == 3
     e.close()
+
+
+def test_fma_probe_reports_plausible_rates():
+    f32 = L.claw_probe_fma(32)
+    f64 = L.claw_probe_fma(64)
+    assert 1e12 < f32 < 3e14
+    assert 1e10 < f64 < f32
