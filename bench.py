@@ -333,8 +333,11 @@ def main():
                              "executed_dflop_per_cell_sweep": 322.0,
                              "executed_frac": 322.0 * ncell / (ms64[dom64] * 1e-3) / fma64}}
 
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()      # the rest is rank 0's single-GPU work
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and rank == 0:
         for key, fn in (("acoustics3d", lambda: extra_acoustics3d(args, peak_gbs)),
                         ("ensembles", lambda: extra_ensembles(args))):
             try:
