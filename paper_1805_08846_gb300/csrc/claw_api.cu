@@ -201,6 +201,34 @@ claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, 
     return CLAW_OK;
 }
 
+// CTAs of direction d's sweep kernel the whole GPU holds at once.
+claw_status resident_ctas(claw_solver* s, int d, int* out) {
+    SweepLaunch L{};
+    L.args = sweep_args(s, d, 0, (int)s->tiles[d].size());
+    L.system = s->system;
+    L.limiter = s->limiter;
+    L.dir = d;
+    L.precision = s->precision;
+    L.grid = 1;
+    L.stream = s->stream;
+    L.resident_out = out;
+    CK(launch_sweep(L));
+    return CLAW_OK;
+}
+
+// Tiles direction d's sweep has with segments of length L (the tail merge
+// of build_tiles aside).
+long long tiles_for_segment(const claw_solver* s, int d, int L) {
+    long long t = 0;
+    for (int i = 0; i < s->B; ++i) {
+        const InstDesc& I = s->inst[i];
+        const long long groups = d == 0 ? ((long long)I.n[1] * I.n[2] + kLines - 1) / kLines
+                                        : (long long)(d == 1 ? I.n[2] : I.n[1]) * ((I.n[0] + kLines - 1) / kLines);
+        t += groups * ((I.n[d] + L - 1) / L);
+    }
+    return t;
+}
+
 // One step attempt for every instance: the sweeps in x, y(, z) order, then
 // the step-control kernel.
 claw_status enqueue_attempt(claw_solver* s) {
@@ -760,11 +788,29 @@ claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
     int best[3] = {s->seg[0], s->seg[1], s->seg[2]};
     claw_status st = CLAW_OK;
     for (int d = 0; d < s->ndim && st == CLAW_OK; ++d) {
-        const int* cand = d == 0 ? cand_x : cand_t;
+        int maxN = 0;
+        for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[d]);
+        // Fixed lengths, plus for w = 1..4 the shortest segment whose tiles
+        // fill at most w waves of resident CTAs (a persistent sweep whose
+        // tiles are few and even ends without a partial last wave).
+        std::vector<int> cand(d == 0 ? cand_x : cand_t, (d == 0 ? cand_x : cand_t) + 9);
+        int resident = 0;
+        st = resident_ctas(s, d, &resident);
+        if (st != CLAW_OK) break;
+        for (int w = 1; w <= 4; ++w) {
+            int lo = 8, hi = (maxN + 7) / 8 * 8;
+            if (tiles_for_segment(s, d, hi) > (long long)w * resident) continue;
+            while (lo < hi) {   // smallest multiple of 8 with few enough tiles
+                const int mid = (lo / 8 + hi / 8) / 2 * 8;
+                if (tiles_for_segment(s, d, mid) <= (long long)w * resident) hi = mid;
+                else lo = mid + 8;
+            }
+            cand.push_back(lo);
+        }
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
         double best_ms = 1e30;
-        for (int k = 0; k < 9 && st == CLAW_OK; ++k) {
-            int maxN = 0;
-            for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[d]);
+        for (size_t k = 0; k < cand.size() && st == CLAW_OK; ++k) {
             if (cand[k] > 2 * maxN && k > 0) break;
             st = claw_set_segment(s, d, cand[k]);
             if (st != CLAW_OK) break;

@@ -16,6 +16,7 @@ struct SweepLaunch {
     bool speeds;     // speeds-only pass (CFL estimate), no update
     unsigned grid;   // CTAs (one per tile)
     cudaStream_t stream;
+    int* resident_out;   // non-null: report the CTAs the GPU holds at once, launch nothing
 };
 
 // Record the thread-local message claw_last_error() returns.

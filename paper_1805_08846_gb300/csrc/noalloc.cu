@@ -212,7 +212,7 @@ extern "C" claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system
     cudaError_t e;
     if (system == CLAW_SHALLOW_WATER) {
         using S = claw::ShallowWater<double>;
-        const S::Params P{params->g, sqrt(params->g)};
+        const S::Params P{params->g, sqrt(params->g), 0.5 * params->g};
         e = na_launch<S>(q, nullptr, nullptr, G, P, scratch, nblk, out, stream);
     } else if (system == CLAW_ACOUSTICS_VAR) {
         using S = claw::Acoustics<double, true>;

@@ -3,6 +3,7 @@
 // the framework maps threads onto interfaces around it).  A new PDE system
 // plugs in by providing one such struct:
 //
+//   Value   arithmetic type: double, float, or f2 (two lines per thread)
 //   NQ      components of the reduced state a sweep touches; component 0 is
 //           the scalar (p or h), 1 the velocity / momentum normal to the
 //           sweep, 2.. transverse components that waves carry
@@ -14,6 +15,9 @@
 //   solve(l, r, P, w)  waves w.W[p][c], speeds w.s[p], fluctuations
 //                      w.amdq[c] (A-dQ), w.apdq[c] (A+dQ)
 //   nonphysical(q)     true for a state the method cannot continue from
+//   zero(p, c)         true where component c of wave p is identically zero
+//                      (products with it are skipped: IEEE rules forbid the
+//                      compiler to drop x * 0 itself)
 //
 // Formulas the paper leaves to its textbook reference are the standard ones:
 // linear acoustics with per-cell impedance, and Roe's linearisation for
@@ -21,6 +25,10 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <type_traits>
+
+#include "pair.cuh"
 
 namespace claw {
 
@@ -53,8 +61,18 @@ template <>
 struct Ops<float> {
     __device__ __forceinline__ static float div(float a, float b) { return __fdividef(a, b); }
     __device__ __forceinline__ static float rcp(float x) { return __fdividef(1.0f, x); }
+    __device__ __forceinline__ static float rsqrt(float x) { return rsqrtf(x); }
     // x > 0: x * rsqrt(x)
     __device__ __forceinline__ static float sqrt_(float x) { return x * rsqrtf(x); }
+};
+template <>
+struct Ops<f2> {
+    __device__ __forceinline__ static f2 div(f2 a, f2 b) {
+        return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+    }
+    __device__ __forceinline__ static f2 rcp(f2 x) { return f2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+    __device__ __forceinline__ static f2 rsqrt(f2 x) { return f2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+    __device__ __forceinline__ static f2 sqrt_(f2 x) { return x * rsqrt(x); }
 };
 
 // ------------------------------------------------------------------------
@@ -69,6 +87,7 @@ struct Ops<float> {
 // ------------------------------------------------------------------------
 template <class Real, bool VAR>
 struct Acoustics {
+    using Value = Real;
     static constexpr int NQ = 2;
     static constexpr int NW = 2;
     static constexpr int NA = VAR ? 2 : 0;
@@ -81,6 +100,7 @@ struct Acoustics {
     };
 
     __device__ __forceinline__ static int field(int d, int comp) { return comp == 0 ? 0 : 1 + d; }
+    __host__ __device__ static constexpr bool zero(int, int) { return false; }
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
         if (!VAR) {
@@ -141,13 +161,14 @@ struct Acoustics {
 // q_m = Q_r - W3.  The sign test of lam_m is done without a square root:
 // for h_m > 0, u_m - sqrt(g h_m) > 0  <=>  hu_m > 0 and hu_m^2 > g h_m^3.
 // ------------------------------------------------------------------------
-template <class Real>
+template <class Real>   // double, float, or f2 (two lines)
 struct ShallowWater {
+    using Value = Real;
     static constexpr int NQ = 3;
     static constexpr int NW = 3;
     static constexpr int NA = 0;
     struct Params {
-        Real g, sqrt_g;
+        Real g, sqrt_g, half_g;
     };
     struct Cell {
         Real q[NQ];
@@ -155,16 +176,18 @@ struct ShallowWater {
         Real sqh;    // sqrt(h)
         Real c;      // sqrt(g h)
     };
-    static constexpr bool kFast = sizeof(Real) == 4;
+    static constexpr bool kFast = !std::is_same<Real, double>::value;
 
     __device__ __forceinline__ static int field(int d, int comp) {
         return comp == 0 ? 0 : (comp == 1 ? 1 + d : 2 - d);
     }
+    // the shear wave W2 = (0, 0, alpha2)
+    __host__ __device__ static constexpr bool zero(int p, int c) { return p == 1 && c < 2; }
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
         if constexpr (kFast) {
             // one reciprocal square root gives sqrt(h) and 1/h
-            const Real r = rsqrtf(cell.q[0]);
+            const Real r = Ops<Real>::rsqrt(cell.q[0]);
             const Real rh = r * r;
             cell.sqh = cell.q[0] * r;
             cell.u = cell.q[1] * rh;
@@ -179,34 +202,38 @@ struct ShallowWater {
         }
     }
 
-    // Roe averages; i2c = 1 / (2 c_hat).
+    // Roe averages; i2c = 1 / (2 c_hat), ni2c = -i2c.
     __device__ __forceinline__ static void roe(const Cell& l, const Cell& r, const Params& P,
-                                               Real& uh, Real& vh, Real& ch, Real& i2c) {
+                                               Real& uh, Real& vh, Real& ch, Real& i2c, Real& ni2c) {
         const Real den = Ops<Real>::rcp(l.sqh + r.sqh);
-        uh = (l.sqh * l.u + r.sqh * r.u) * den;
-        vh = (l.sqh * l.v + r.sqh * r.v) * den;
-        const Real gh = P.g * (Real(0.5) * (l.q[0] + r.q[0]));
+        uh = vfma(l.sqh, l.u, r.sqh * r.u) * den;
+        vh = vfma(l.sqh, l.v, r.sqh * r.v) * den;
+        const Real gh = P.half_g * (l.q[0] + r.q[0]);   // 0.5 g exactly: g (0.5 s) = (0.5 g) s
         if constexpr (kFast) {
-            const Real rc = rsqrtf(gh);
+            const Real rc = Ops<Real>::rsqrt(gh);
             ch = gh * rc;
-            i2c = Real(0.5) * rc;
+            i2c = Real(0.5f) * rc;
+            ni2c = Real(-0.5f) * rc;
         } else {
             ch = sqrt(gh);
             i2c = Real(0.5) / ch;
+            ni2c = -i2c;
         }
     }
 
     __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
                                                  Waves<Real, NQ, NW>& w) {
-        Real uh, vh, ch, i2c;
-        roe(l, r, P, uh, vh, ch, i2c);
-        const Real d0 = r.q[0] - l.q[0];
+        Real uh, vh, ch, i2c, ni2c;
+        roe(l, r, P, uh, vh, ch, i2c, ni2c);
+        // strengths with nd0 = -(h_r - h_l) so that no operand needs negating:
+        //   a1 = (s3 d0 - d1) / 2c,  a2 = d2 - vh d0,  a3 = (d1 - s1 d0) / 2c
+        const Real nd0 = l.q[0] - r.q[0];
         const Real d1 = r.q[1] - l.q[1];
         const Real d2 = r.q[2] - l.q[2];
         const Real s1 = uh - ch, s3 = uh + ch;
-        const Real a1 = (s3 * d0 - d1) * i2c;
-        const Real a2 = d2 - vh * d0;
-        const Real a3 = (d1 - s1 * d0) * i2c;
+        const Real a1 = vfma(s3, nd0, d1) * ni2c;
+        const Real a2 = vfma(vh, nd0, d2);
+        const Real a3 = vfma(s1, nd0, d1) * i2c;
         w.s[0] = s1;
         w.s[1] = uh;
         w.s[2] = s3;
@@ -221,43 +248,49 @@ struct ShallowWater {
         w.W[2][2] = a3 * vh;
 
         // Split factors: A-dQ = sum km_p W_p, A+dQ = sum kp_p W_p.
-        Real km1 = fmin(s1, Real(0)), kp1 = fmax(s1, Real(0));
-        Real km3 = fmin(s3, Real(0)), kp3 = fmax(s3, Real(0));
-        const Real km2 = fmin(uh, Real(0)), kp2 = fmax(uh, Real(0));
+        Real km1 = vmin(s1, Real(0)), kp1 = vmax(s1, Real(0));
+        Real km3 = vmin(s3, Real(0)), kp3 = vmax(s3, Real(0));
+        const Real km2 = vmin(uh, Real(0)), kp2 = vmax(uh, Real(0));
 
         const Real lam_l = l.u - l.c;
-        if (lam_l < Real(0)) {
+        const auto left = vlt(lam_l, Real(0));
+        if (any(left)) {
             const Real hm = l.q[0] + w.W[0][0];
             const Real hum = l.q[1] + w.W[0][1];
-            if (hm > Real(0) && hum > Real(0) && hum * hum > P.g * hm * hm * hm) {
+            const auto fix = left & vgt(hm, Real(0)) & vgt(hum, Real(0)) & vgt(hum * hum, P.g * hm * hm * hm);
+            if (any(fix)) {
                 const Real lam_m = Ops<Real>::div(hum, hm) - Ops<Real>::sqrt_(P.g * hm);
                 const Real beta = Ops<Real>::div(lam_m - s1, lam_m - lam_l);
-                km1 = beta * lam_l;
-                kp1 = (Real(1) - beta) * lam_m;
+                km1 = sel(fix, beta * lam_l, km1);
+                kp1 = sel(fix, (Real(1) - beta) * lam_m, kp1);
             }
         }
         const Real lam_r = r.u + r.c;
-        if (lam_r > Real(0)) {
+        const auto right = vgt(lam_r, Real(0));
+        if (any(right)) {
             const Real hm = r.q[0] - w.W[2][0];
             const Real hum = r.q[1] - w.W[2][1];
-            if (hm > Real(0) && hum < Real(0) && hum * hum > P.g * hm * hm * hm) {
+            const auto fix = right & vgt(hm, Real(0)) & vlt(hum, Real(0)) & vgt(hum * hum, P.g * hm * hm * hm);
+            if (any(fix)) {
                 const Real lam_m = Ops<Real>::div(hum, hm) + Ops<Real>::sqrt_(P.g * hm);
                 const Real beta = Ops<Real>::div(lam_r - s3, lam_r - lam_m);
-                km3 = beta * lam_m;
-                kp3 = (Real(1) - beta) * lam_r;
+                km3 = sel(fix, beta * lam_m, km3);
+                kp3 = sel(fix, (Real(1) - beta) * lam_r, kp3);
             }
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) {
-            w.amdq[c] = km1 * w.W[0][c] + km2 * w.W[1][c] + km3 * w.W[2][c];
-            w.apdq[c] = kp1 * w.W[0][c] + kp2 * w.W[1][c] + kp3 * w.W[2][c];
+        for (int c = 0; c < 2; ++c) {
+            w.amdq[c] = vfma(km1, w.W[0][c], km3 * w.W[2][c]);
+            w.apdq[c] = vfma(kp1, w.W[0][c], kp3 * w.W[2][c]);
         }
+        w.amdq[2] = vfma(km1, w.W[0][2], vfma(km2, w.W[1][2], km3 * w.W[2][2]));
+        w.apdq[2] = vfma(kp1, w.W[0][2], vfma(kp2, w.W[1][2], kp3 * w.W[2][2]));
     }
 
     __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params& P,
                                                   Real s[NW]) {
-        Real uh, vh, ch, i2c;
-        roe(l, r, P, uh, vh, ch, i2c);
+        Real uh, vh, ch, i2c, ni2c;
+        roe(l, r, P, uh, vh, ch, i2c, ni2c);
         s[0] = uh - ch;
         s[1] = uh;
         s[2] = uh + ch;
@@ -265,13 +298,13 @@ struct ShallowWater {
 
     // max_p |s_p| = max(|u_hat - c_hat|, |u_hat + c_hat|) (c_hat >= 0 bounds |u_hat|).
     __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) {
-        return fmax(fabs(w.s[0]), fabs(w.s[2]));
+        return vmax(vabs(w.s[0]), vabs(w.s[2]));
     }
 
     // h <= 0 or NaN stops the run; a non-finite momentum makes the next
     // sweep's speeds non-finite, which the step control catches.
-    __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
-        return !(q[0] > Real(0) && q[0] <= (Real)3.0e38);
+    __device__ __forceinline__ static auto nonphysical(const Real q[NQ]) {
+        return !(vgt(q[0], Real(0)) & vle(q[0], Real(3.0e38)));
     }
     // Cheaper form for the sweep: fold h's bit pattern into a running
     // signed-integer minimum; a minimum <= 0 means some h <= 0 (a NaN h
@@ -300,7 +333,9 @@ __device__ __forceinline__ Real limiter_phi(Real theta) {
 // zero wave saturates to 0).  FP64: the correctly rounded ratio.
 template <int LIM, class Real>
 __device__ __forceinline__ Real limiter_ratio(Real num, Real den) {
-    if constexpr (sizeof(Real) == 4) {
+    if constexpr (std::is_same<Real, f2>::value) {
+        return f2(limiter_ratio<LIM, float>(num.v.x, den.v.x), limiter_ratio<LIM, float>(num.v.y, den.v.y));
+    } else if constexpr (sizeof(Real) == 4) {
         const float theta = num * __fdividef(1.0f, den);
         if (LIM == kLimMinmod) return __saturatef(theta);
         if (LIM == kLimMC) return 2.0f * __saturatef(fminf(theta, 0.25f + 0.25f * theta));

@@ -179,27 +179,33 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
 // 16-byte reads of its own rows hit every bank once.
 template <class Sys, class Real, int DIR>
 struct StageCfg {
+    // lines per thread: 2 when the system computes on f2 (two FP32 lines)
+    static constexpr int PK = Lanes<typename Sys::Value>::N;
+    static constexpr int NT = kLines / PK;                      // threads per CTA
     static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
     static constexpr int G = 16 / (int)sizeof(Real);            // cells per 16-byte half
     static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
-    static constexpr int STAGES = 3;
+    static constexpr int STAGES = PK == 2 ? 2 : 3;
     // x sweep results leave through their input stages and bulk stores
     // (measured: direct stores from 32 rows per warp are 3x slower)
     static constexpr bool XWB = true;
     static constexpr int STAGE_BYTES = NP * BOX;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
     // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
-    // a 5-CTA budget forces worse schedules), 2 for FP64
-    static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 4 : 2;
+    // a 5-CTA budget forces worse schedules), 2 for FP64; 5 CTAs of 64
+    // two-line threads for the packed form
+    static constexpr int MIN_CTAS = PK == 2 ? 6 : (sizeof(Real) == 4 ? 4 : 2);
 };
 
 template <class Sys, class Real, int LIM, int DIR>
-__global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
+__global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     sweep_kernel(const SweepArgs A, const typename Sys::Params P) {
     using Cfg = StageCfg<Sys, Real, DIR>;
+    using V = typename Sys::Value;     // Real, or f2 for two lines per thread
+    constexpr int PK = Cfg::PK;
     using Cell = typename Sys::Cell;
-    using W = Waves<Real, Sys::NQ, Sys::NW>;
+    using W = Waves<typename Sys::Value, Sys::NQ, Sys::NW>;
     constexpr int NQ = Sys::NQ;
     constexpr int NW = Sys::NW;
     constexpr int NA = Sys::NA;
@@ -235,15 +241,21 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     Control* ctl = A.ctl + td.inst;
     if (*(volatile int*)&ctl->active == 0) continue;
 
-    const int lane = threadIdx.x;
-    long long base, stride;
-    const bool valid = line_geometry<DIR>(td, I, lane, base, stride);
+    // Line slot k of this thread: the tile line it marches.  x sweep: rows t
+    // and t + 64 (a warp reads 32 consecutive rows per access); y, z: the
+    // adjacent lines 2t, 2t + 1 (one 8-byte access covers both).
+    auto line_of = [](int k) { return DIR == 0 ? (int)threadIdx.x + k * Cfg::NT : (int)threadIdx.x * PK + k; };
+    long long base[PK], stride = 0;
+    bool valid[PK];
+#pragma unroll
+    for (int k = 0; k < PK; ++k) valid[k] = line_geometry<DIR>(td, I, line_of(k), base[k], stride);
     const int N = I.n[DIR];
     const int bc_lo = I.bc[2 * DIR], bc_hi = I.bc[2 * DIR + 1];
     const int a = td.a, b = td.b;
     const int nchunks = (b - a + C - 1) / C;
 
-    // Version slots: TMA plane index and direct pointers for each component.
+    // Version slots: TMA plane index and field-plane pointers for each
+    // component (a cell of line slot k sits at base[k] + i * stride).
     Real* pool = static_cast<Real*>(A.pool);
     int plane[NP], plane_out[NQ];
     const Real* qin[NQ];
@@ -256,13 +268,13 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         const int sout = (cur + A.slots.out_off[f]) % 3;
         plane[c] = sin * A.m + f;
         plane_out[c] = sout * A.m + f;
-        qin[c] = pool + I.offset + sin * I.vstride + f * I.fstride + base;
-        qout[c] = pool + I.offset + sout * I.vstride + f * I.fstride + base;
+        qin[c] = pool + I.offset + sin * I.vstride + f * I.fstride;
+        qout[c] = pool + I.offset + sout * I.vstride + f * I.fstride;
     }
 #pragma unroll
     for (int k = 0; k < NA; ++k) plane[NQ + k] = k;
     const Real* aux = nullptr;
-    if (NA > 0) aux = static_cast<const Real*>(A.aux) + I.aux_offset + base;
+    if (NA > 0) aux = static_cast<const Real*>(A.aux) + I.aux_offset;
     const CUtensorMap* smap = &A.tma[td.inst].map[DIR];
     const CUtensorMap* amap = &A.tma[td.inst].map[3 + DIR];
 
@@ -286,30 +298,29 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     }
 
     // Direct load of cell k (ghost or interior) for the segment's ends.
-    auto load_direct = [&](int k, Cell& cell) {
-        if (valid) {
-            bool flip;
-            const int j = map_cell(k, N, bc_lo, bc_hi, flip);
-            const long long o = (long long)j * stride;
+    // (lines past the grid edge march a harmless constant state)
+    auto load_direct = [&](int kc, Cell& cell) {
+        bool flip;
+        const int j = map_cell(kc, N, bc_lo, bc_hi, flip);
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) cell.q[c] = __ldg(qin[c] + o);
-            if (flip) cell.q[1] = -cell.q[1];
-            if constexpr (NA > 0) {
-                cell.Z = __ldg(aux + o);
-                cell.c = __ldg(aux + I.fstride + o);
+        for (int k = 0; k < PK; ++k) {
+            const long long o = base[k] + (long long)j * stride;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                Real x = valid[k] ? __ldg(qin[c] + o) : Real(1);
+                if (c == 1 && flip) x = -x;
+                set_lane(cell.q[c], k, x);
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) cell.q[c] = Real(1);
             if constexpr (NA > 0) {
-                cell.Z = Real(1);
-                cell.c = Real(1);
+                set_lane(cell.Z, k, valid[k] ? __ldg(aux + o) : Real(1));
+                set_lane(cell.c, k, valid[k] ? __ldg(aux + I.fstride + o) : Real(1));
             }
         }
         Sys::prepare(cell, P);
     };
 
-    const Real nu = (Real)(ctl->dt_attempt / I.dx[DIR]);
+    const Real nu_s = (Real)(ctl->dt_attempt / I.dx[DIR]);
+    const V nu = V(nu_s), nnu = V(-nu_s);
     SM smax = 0;
     bool bad = false;
     int hbits = 0x7fffffff;   // running minimum of h's (high) bit pattern
@@ -322,62 +333,79 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     //   F0     correction flux at interface I-1;  qkeep  state of cell I-1
     Cell prev;
     W wB;
-    Real ssB[NW], dAB[NW], apdqA[NQ], F0[NQ], qkeep[NQ];
+    V ssB[NW], dAB[NW], apdqA[NQ], F0[NQ], qkeep[NQ];
 
     auto dot = [](const W& x, const W& y, int p) {
-        Real d = Real(0);
+        V d = V(0);
+        bool first = true;
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) d += x.W[p][c] * y.W[p][c];
+        for (int c = 0; c < NQ; ++c)
+            if (!Sys::zero(p, c)) {
+                d = first ? x.W[p][c] * y.W[p][c] : vfma(x.W[p][c], y.W[p][c], d);
+                first = false;
+            }
         return d;
     };
     // Limited correction flux at interface I (waves wB, ratios from the
     // upwind side: I-1 when s > 0, else I+1).
-    auto flux = [&](const Real* d_up_left, const Real* d_up_right, Real* F) {
+    auto flux = [&](const V* d_up_left, const V* d_up_right, V* F) {
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) F[c] = Real(0);
+        for (int c = 0; c < NQ; ++c) F[c] = V(0);
 #pragma unroll
         for (int p = 0; p < NW; ++p) {
-            const Real sp = wB.s[p];
-            Real phi = Real(1);
+            const V sp = wB.s[p];
+            V phi = V(1);
             if (LIM != kLimNone) {
-                const Real num = sp > Real(0) ? d_up_left[p] : d_up_right[p];
-                phi = limiter_ratio<LIM, Real>(num, ssB[p]);
+                const V num = sel(vgt(sp, V(0)), d_up_left[p], d_up_right[p]);
+                phi = limiter_ratio<LIM, V>(num, ssB[p]);
             }
-            const Real as = fabs(sp);
-            const Real k = Real(0.5) * as * (Real(1) - nu * as) * phi;
+            const V as = vabs(sp);
+            const V k = V(0.5f) * as * vfma(nnu, as, V(1)) * phi;   // 1/2 |s| (1 - nu |s|) phi
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) F[c] += k * wB.W[p][c];
+            for (int c = 0; c < NQ; ++c)
+                if (!Sys::zero(p, c)) F[c] = vfma(k, wB.W[p][c], F[c]);
         }
     };
     // Consume cell I+1: solve interface I+1, limit interface I, form the new
     // state qn of cell I-1.  SPEED: interface I+1 bounds an interior cell of
     // the segment.  UPDATE: cell I-1 belongs to the segment.
-    auto step = [&](const Cell& cur, bool speed, bool update, Real* qn) {
+    auto step = [&](const Cell& cur, bool speed, bool update, V* qn) {
         W wC;
         Sys::solve(prev, cur, P, wC);
-        if (valid && speed) smax = max(smax, speed_bits(Sys::max_speed(wC)));
-        Real dBC[NW], ssC[NW];
+        if (speed) {
+            const V ms = Sys::max_speed(wC);
+#pragma unroll
+            for (int k = 0; k < PK; ++k)
+                if (valid[k]) smax = max(smax, speed_bits(lane_of(ms, k)));
+        }
+        V dBC[NW], ssC[NW];
 #pragma unroll
         for (int p = 0; p < NW; ++p) {
             dBC[p] = dot(wB, wC, p);
             ssC[p] = dot(wC, wC, p);
         }
-        Real F1[NQ];
+        V F1[NQ];
         flux(dAB, dBC, F1);
         if (update) {
 #pragma unroll
             for (int c = 0; c < NQ; ++c) {
-                const Real first = apdqA[c] + wB.amdq[c];
-                const Real second = F1[c] - F0[c];
-                qn[c] = qkeep[c] - nu * first - nu * second;
+                const V first = apdqA[c] + wB.amdq[c];
+                const V second = F1[c] - F0[c];
+                qn[c] = vfma(nnu, second, vfma(nnu, first, qkeep[c]));
             }
-            if (valid) {
-                if constexpr (Sys::kMinH) {
-                    if constexpr (sizeof(Real) == 4) hbits = min(hbits, __float_as_int(qn[0]));
-                    else hbits = min(hbits, (int)(__double_as_longlong(qn[0]) >> 32));
-                } else {
-                    bad |= Sys::nonphysical(qn);
+            if constexpr (Sys::kMinH) {
+#pragma unroll
+                for (int k = 0; k < PK; ++k) {
+                    const Real h = lane_of(qn[0], k);
+                    int hb;
+                    if constexpr (sizeof(Real) == 4) hb = __float_as_int(h);
+                    else hb = (int)(__double_as_longlong(h) >> 32);
+                    if (valid[k]) hbits = min(hbits, hb);
                 }
+            } else {
+                const auto np = Sys::nonphysical(qn);
+#pragma unroll
+                for (int k = 0; k < PK; ++k) bad |= valid[k] && lane_of(np, k);
             }
         }
 #pragma unroll
@@ -405,7 +433,12 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         Sys::solve(c0, c1, P, wX);                    // interface a-1
         load_direct(a, c0);
         Sys::solve(c1, c0, P, wB);                    // interface a
-        if (valid) smax = max(smax, speed_bits(Sys::max_speed(wB)));
+        {
+            const V ms = Sys::max_speed(wB);
+#pragma unroll
+            for (int k = 0; k < PK; ++k)
+                if (valid[k]) smax = max(smax, speed_bits(lane_of(ms, k)));
+        }
 #pragma unroll
         for (int p = 0; p < NW; ++p) {
             dAB[p] = dot(wX, wB, p);
@@ -413,42 +446,59 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         }
 #pragma unroll
         for (int c = 0; c < NQ; ++c) {
-            F0[c] = Real(0);
+            F0[c] = V(0);
             apdqA[c] = wX.apdq[c];
             qkeep[c] = c1.q[c];
         }
         prev = c0;                                     // cell a
         load_direct(a + 1, c1);
-        Real unused[NQ];
+        V unused[NQ];
         step(c1, true, false, unused);                // interface a+1, flux at a
     }
 
     // y, z sweeps: the new state of cell i goes straight to global memory (a
     // warp writes 32 consecutive x, whole 128-byte lines).
-    auto put_global = [&](int i, const Real* qn) {
-        if (valid) {
+    auto put_global = [&](int i, const V* qn) {
+        if constexpr (PK == 2 && DIR != 0) {
+            const long long o = base[0] + (long long)i * stride;   // even: 8-byte aligned
+            if (valid[1]) {
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) qout[c][(long long)i * stride] = qn[c];
+                for (int c = 0; c < NQ; ++c) *reinterpret_cast<float2*>(qout[c] + o) = qn[c].v;
+            } else if (valid[0]) {
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) qout[c][o] = qn[c].v.x;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < PK; ++k)
+                if (valid[k]) {
+#pragma unroll
+                    for (int c = 0; c < NQ; ++c) qout[c][base[k] + (long long)i * stride] = lane_of(qn[c], k);
+                }
         }
     };
     constexpr int G = Cfg::G;
-    const int sw = (lane >> 2) & 1;    // 32-byte swizzle of row `lane`
 
     // x sweep: results go back into the input stage they came from (each
     // result overwrites an input position already consumed) and leave by
     // bulk-tensor stores, so the staging buffers serve both ways (a warp's
     // direct stores would touch 32 rows).  Byte offset of chunk position jj
     // of line `lane` inside a plane box:
-    auto pos_off = [&](int jj) {
-        return DIR == 0 ? lane * 32 + 16 * ((jj / G) ^ sw) + (jj % G) * (int)sizeof(Real)
-                        : (jj * kLines + lane) * (int)sizeof(Real);
+    // (the 32-byte swizzle of row r swaps its halves on bit 2 of r)
+    auto pos_off = [&](int line, int jj) {
+        return DIR == 0 ? line * 32 + 16 * ((jj / G) ^ ((line >> 2) & 1)) + (jj % G) * (int)sizeof(Real)
+                        : (jj * kLines + line) * (int)sizeof(Real);
     };
     auto stage_of = [&](int kk) { return smem + ((kbase + kk) % STAGES) * Cfg::STAGE_BYTES; };
-    auto put_stage = [&](int i, const Real* qn) {
+    auto put_stage = [&](int i, const V* qn) {
         const int rel = i - a;
-        unsigned char* st = stage_of(rel / C) + pos_off(rel % C);
+        unsigned char* st = stage_of(rel / C);
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(st + c * Cfg::BOX) = qn[c];
+        for (int k = 0; k < PK; ++k) {
+            unsigned char* sk = st + pos_off(line_of(k), rel % C);
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(sk + c * Cfg::BOX) = lane_of(qn[c], k);
+        }
     };
     auto store_stage = [&](int kk) {       // thread 0
         const unsigned char* st = stage_of(kk);
@@ -474,7 +524,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         const int jhi = min(C, b - (a + k * C));       // cells from b on come directly
         // Cells come straight from shared memory as they are marched over;
         // the stage is released once the whole chunk has been consumed.
-        auto make_cell = [&](const Real* vals, Cell& cur) {
+        auto make_cell = [&](const V* vals, Cell& cur) {
 #pragma unroll
             for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
             if constexpr (NA > 0) {
@@ -488,13 +538,24 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
         // chunk that has already been consumed.
 #pragma unroll 2
         for (int j = jlo; j < jhi; ++j) {
-            const int off = pos_off(j);
-            Real vals[NP];
+            V vals[NP];
+            if constexpr (PK == 2 && DIR != 0) {
+                const int off = pos_off(line_of(0), j);
 #pragma unroll
-            for (int p = 0; p < NP; ++p) vals[p] = *reinterpret_cast<const Real*>(stage + p * Cfg::BOX + off);
+                for (int p = 0; p < NP; ++p)
+                    vals[p] = V(*reinterpret_cast<const float2*>(stage + p * Cfg::BOX + off));
+            } else {
+#pragma unroll
+                for (int k = 0; k < PK; ++k) {
+                    const int off = pos_off(line_of(k), j);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        set_lane(vals[p], k, *reinterpret_cast<const Real*>(stage + p * Cfg::BOX + off));
+                }
+            }
             Cell cur;
             make_cell(vals, cur);
-            Real qn[NQ];
+            V qn[NQ];
             step(cur, true, true, qn);
             if (DIR != 0 || !Cfg::XWB) {
                 put_global(a + k * C + j - 2, qn);
@@ -548,7 +609,7 @@ __global__ void __launch_bounds__(kLines, (StageCfg<Sys, Real, DIR>::MIN_CTAS))
     // interior cell of the segment.
     {
         Cell c1;
-        Real qn[NQ];
+        V qn[NQ];
         load_direct(b, c1);
         step(c1, true, true, qn);
         if (DIR == 0 && Cfg::XWB) put_stage(b - 2, qn); else put_global(b - 2, qn);

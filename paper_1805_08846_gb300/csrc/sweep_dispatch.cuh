@@ -16,16 +16,20 @@ cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR>, kLines,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR>, Cfg::NT,
                                                           Cfg::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         resident = per_sm * sms > 0 ? per_sm * sms : 1;
     }
+    if (L.resident_out) {
+        *L.resident_out = resident;
+        return cudaSuccess;
+    }
     unsigned grid = L.grid;
     if (L.args.persistent && grid > (unsigned)resident) grid = (unsigned)resident;
-    sweep_kernel<Sys, Real, LIM, DIR><<<grid, kLines, Cfg::SMEM, L.stream>>>(L.args, P);
+    sweep_kernel<Sys, Real, LIM, DIR><<<grid, Cfg::NT, Cfg::SMEM, L.stream>>>(L.args, P);
     return cudaGetLastError();
 }
 
@@ -36,23 +40,28 @@ cudaError_t speed_go(const SweepLaunch& L, const typename Sys::Params& P) {
     return cudaGetLastError();
 }
 
-template <class Sys, class Real, int DIR>
-cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P) {
+// Sys: the system of the speeds-only pass and of the x sweep (scalar Real);
+// SysT: the system the y and z sweeps compute with (Sys itself, or its
+// two-line f2 form).
+template <class Sys, class SysS, class Real, int DIR>
+cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P,
+                             const typename SysS::Params& PS) {
     if (L.speeds) return speed_go<Sys, Real, DIR>(L, P);
     switch (L.limiter) {
-        case kLimNone: return sweep_go<Sys, Real, kLimNone, DIR>(L, P);
-        case kLimMinmod: return sweep_go<Sys, Real, kLimMinmod, DIR>(L, P);
-        default: return sweep_go<Sys, Real, kLimMC, DIR>(L, P);
+        case kLimNone: return sweep_go<SysS, Real, kLimNone, DIR>(L, PS);
+        case kLimMinmod: return sweep_go<SysS, Real, kLimMinmod, DIR>(L, PS);
+        default: return sweep_go<SysS, Real, kLimMC, DIR>(L, PS);
     }
 }
 
-template <class Sys, class Real, bool HAS_Z>
-cudaError_t sweep_by_dir(const SweepLaunch& L, const typename Sys::Params& P) {
+template <class Sys, class Real, bool HAS_Z, class SysT = Sys>
+cudaError_t sweep_by_dir(const SweepLaunch& L, const typename Sys::Params& P,
+                         const typename SysT::Params& PT) {
     switch (L.dir) {
-        case 0: return sweep_by_limiter<Sys, Real, 0>(L, P);
-        case 1: return sweep_by_limiter<Sys, Real, 1>(L, P);
+        case 0: return sweep_by_limiter<Sys, Sys, Real, 0>(L, P, P);
+        case 1: return sweep_by_limiter<Sys, SysT, Real, 1>(L, P, PT);
         default:
-            if constexpr (HAS_Z) return sweep_by_limiter<Sys, Real, 2>(L, P);
+            if constexpr (HAS_Z) return sweep_by_limiter<Sys, SysT, Real, 2>(L, P, PT);
             return cudaErrorInvalidValue;
     }
 }

@@ -1,4 +1,7 @@
-// Sweep kernels: shallow water (Roe + Harten-Hyman), float, 2D only.
+// Sweep kernels: shallow water (Roe + Harten-Hyman), float, 2D only.  The y
+// sweep marches two lines per thread on packed FP32 pairs (f2); the x sweep
+// (whose results return through its staging ring, three stages deep, which
+// leaves room for too few two-line CTAs) and the speeds-only pass stay scalar.
 #include <math.h>
 
 #include "sweep_dispatch.cuh"
@@ -6,7 +9,10 @@
 namespace claw {
 cudaError_t launch_sweep_shallow_water_f32(const SweepLaunch& L) {
     using S = ShallowWater<float>;
-    const S::Params P{(float)L.args.g, (float)sqrt(L.args.g)};
-    return sweep_by_dir<S, float, false>(L, P);
+    using S2 = ShallowWater<f2>;
+    const float g = (float)L.args.g, sg = (float)sqrt(L.args.g), hg = (float)(0.5 * L.args.g);
+    const S::Params P{g, sg, hg};
+    const S2::Params P2{f2(g), f2(sg), f2(hg)};
+    return sweep_by_dir<S, float, false, S2>(L, P, P2);
 }
 }  // namespace claw
