@@ -358,7 +358,20 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
     const InstDesc& I = s->inst[i];
     const CUtensorMapDataType dt = s->precision == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t es = s->esize;
-    const cuuint32_t cx = (cuuint32_t)(32 / es);   // 32-byte rows for the x sweep
+    // x sweep boxes: the kernel's chunk of each row (32 bytes: swizzled)
+    int chunk = 0;
+    {
+        SweepLaunch L{};
+        L.system = s->system;
+        L.limiter = s->limiter;
+        L.dir = 0;
+        L.precision = s->precision;
+        L.grid = 1;
+        L.chunk_out = &chunk;
+        CK(launch_sweep(L));
+    }
+    const cuuint32_t cx = (cuuint32_t)chunk;
+    const CUtensorMapSwizzle xsw = cx * es == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
     const cuuint32_t ct = (cuuint32_t)(32 / es);   // cells per chunk along y / z (4 KB boxes)
     for (int kind = 0; kind < 2; ++kind) {
         if (kind == 1 && s->system != CLAW_ACOUSTICS_VAR) break;
@@ -368,7 +381,7 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
             const cuuint64_t dims[3] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1] * I.n[2], planes};
             const cuuint64_t str[2] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.fstride * es};
             const cuuint32_t box[3] = {cx, (cuuint32_t)kLines, 1};
-            CKS(encode(&T.map[3 * kind + 0], dt, 3, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B));
+            CKS(encode(&T.map[3 * kind + 0], dt, 3, base, dims, str, box, xsw));
         }
         const cuuint64_t dims[4] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1], (cuuint64_t)I.n[2], planes};
         const cuuint64_t str[3] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.n[1] * I.pitch * es,

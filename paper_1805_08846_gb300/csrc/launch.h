@@ -17,6 +17,7 @@ struct SweepLaunch {
     unsigned grid;   // CTAs (one per tile)
     cudaStream_t stream;
     int* resident_out;   // non-null: report the CTAs the GPU holds at once, launch nothing
+    int* chunk_out;      // non-null: report the cells per staged chunk, launch nothing
 };
 
 // Record the thread-local message claw_last_error() returns.

@@ -186,15 +186,19 @@ struct StageCfg {
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
     static constexpr int G = 16 / (int)sizeof(Real);            // cells per 16-byte half
     static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
-    static constexpr int STAGES = PK == 2 ? 2 : 3;
+    // y, z: two stages suffice for the two-line form (more CTAs fit); the x
+    // sweep refills a stage only after the write-back of the chunk before
+    // has read it, which needs three
+    static constexpr int STAGES = (PK == 2 && DIR != 0) ? 2 : 3;
     // x sweep results leave through their input stages and bulk stores
     // (measured: direct stores from 32 rows per warp are 3x slower)
     static constexpr bool XWB = true;
+    static_assert(DIR != 0 || !XWB || STAGES >= 3, "the x write-back ring needs three stages");
     static constexpr int STAGE_BYTES = NP * BOX;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
     // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
-    // a 5-CTA budget forces worse schedules), 2 for FP64; 5 CTAs of 64
-    // two-line threads for the packed form
+    // a 5-CTA budget forces worse schedules), 2 for FP64; 6 CTAs of 64
+    // two-line threads for the packed form (7 fit at run time)
     static constexpr int MIN_CTAS = PK == 2 ? 6 : (sizeof(Real) == 4 ? 4 : 2);
 };
 

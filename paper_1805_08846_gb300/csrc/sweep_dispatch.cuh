@@ -10,6 +10,10 @@ template <class Sys, class Real, int LIM, int DIR>
 cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     if (L.grid == 0) return cudaSuccess;
     using Cfg = StageCfg<Sys, Real, DIR>;
+    if (L.chunk_out) {
+        *L.chunk_out = Cfg::C;
+        return cudaSuccess;
+    }
     static int resident = 0;   // CTAs of this kernel the whole GPU holds at once
     if (!resident) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
@@ -40,8 +44,8 @@ cudaError_t speed_go(const SweepLaunch& L, const typename Sys::Params& P) {
     return cudaGetLastError();
 }
 
-// Sys: the system of the speeds-only pass and of the x sweep (scalar Real);
-// SysT: the system the y and z sweeps compute with (Sys itself, or its
+// Sys: the system of the speeds-only pass (scalar Real); SysX, SysT: the
+// systems the x and the y, z sweeps compute with (Sys itself, or its
 // two-line f2 form).
 template <class Sys, class SysS, class Real, int DIR>
 cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P,
@@ -54,11 +58,11 @@ cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P
     }
 }
 
-template <class Sys, class Real, bool HAS_Z, class SysT = Sys>
+template <class Sys, class Real, bool HAS_Z, class SysX = Sys, class SysT = Sys>
 cudaError_t sweep_by_dir(const SweepLaunch& L, const typename Sys::Params& P,
-                         const typename SysT::Params& PT) {
+                         const typename SysX::Params& PX, const typename SysT::Params& PT) {
     switch (L.dir) {
-        case 0: return sweep_by_limiter<Sys, Sys, Real, 0>(L, P, P);
+        case 0: return sweep_by_limiter<Sys, SysX, Real, 0>(L, P, PX);
         case 1: return sweep_by_limiter<Sys, SysT, Real, 1>(L, P, PT);
         default:
             if constexpr (HAS_Z) return sweep_by_limiter<Sys, SysT, Real, 2>(L, P, PT);

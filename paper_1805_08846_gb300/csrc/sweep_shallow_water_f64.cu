@@ -7,6 +7,6 @@ namespace claw {
 cudaError_t launch_sweep_shallow_water_f64(const SweepLaunch& L) {
     using S = ShallowWater<double>;
     const S::Params P{(double)L.args.g, (double)sqrt(L.args.g), 0.5 * L.args.g};
-    return sweep_by_dir<S, double, false>(L, P, P);
+    return sweep_by_dir<S, double, false>(L, P, P, P);
 }
 }  // namespace claw
