@@ -13,6 +13,8 @@ oracle instead (the reference arm).
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import platform
@@ -34,6 +36,37 @@ METRIC = "cell-updates/s"
 # FP64 sweep executes 322 (double divide / square root expand into FMA
 # sequences) -- both counted with ncu, see profiles/.
 SW_FLOP_PER_CELL_SWEEP = 313.0 / 2.0
+
+
+def kernel_source_digest():
+    """Digest of the CUDA sources: a traffic record taken with ncu is valid
+    only for the kernels it was taken on."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_08846_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summaries (a line `traffic-record: kernel=... workload=... sources=...
+    dram_bytes=...`), or None when no record matches the current sources."""
+    digest = kernel_source_digest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if kv.get("kernel") == kernel and kv.get("workload") == workload \
+                        and kv.get("sources") == digest:
+                    return float(kv["dram_bytes"]), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def load_peaks():
@@ -250,6 +283,8 @@ def main():
                     help="skip the 3D acoustics and ensemble measurements")
     ap.add_argument("--n3", type=int, default=512)
     ap.add_argument("--steps3", type=int, default=20)
+    ap.add_argument("--segments", default=None,
+                    help="fixed FP32 segment lengths 'x,y' instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -274,7 +309,12 @@ def main():
 
     def timed(precision):
         s = Solver.from_problem(prob, precision=precision, stream="torch")
-        segs[precision] = s.autotune(2)               # tile shapes (state restored)
+        if precision == 32 and args.segments:
+            segs[precision] = [int(v) for v in args.segments.split(",")][:2]
+            for d, L_ in enumerate(segs[precision]):
+                s.set_segment(d, L_)
+        else:
+            segs[precision] = s.autotune(2)           # tile shapes (state restored)
         s.run_steps(args.warmup)                      # warm-up: graphs, caches, clocks
         barrier(world)
         torch.cuda.synchronize()
@@ -297,6 +337,8 @@ def main():
     bytes_per_launch = 6 * 4 * ncell
     dom = 0 if ms32[0] >= ms32[1] else 1
     achieved = bytes_per_launch / (ms32[dom] * 1e-3) / 1e9
+    dom_kernel = f"sweep_kernel<ShallowWater<float>,minmod,dir={'xy'[dom]}>"
+    traffic, traffic_src = traffic_record(dom_kernel, f"sw_dam_break_{N}")
 
     # End to end through the public API with pinned host buffers.
     q_host = torch.from_numpy(prob.q0).pin_memory()
@@ -359,8 +401,9 @@ def main():
                    "l2": "inputs larger than L2 (201 MB per FP32 state version vs 129 MB L2)",
                    "segments": {"f32": segs.get(32, [])[:2], "f64": segs.get(64, [])[:2]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                     "frac": achieved / peak_gbs, "traffic": None,
-                     "kernel": f"sweep_kernel<ShallowWater<float>, minmod, dir={'xy'[dom]}>",
+                     "frac": achieved / peak_gbs, "traffic": traffic,
+                     "traffic_source": traffic_src, "algorithmic_bytes": bytes_per_launch,
+                     "kernel": dom_kernel,
                      "peak_kind": f"{peak_kind} (copy)",
                      "sweep_ms": {"x": ms32[0], "y": ms32[1], "control": ms32[3]}},
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / args.steps,

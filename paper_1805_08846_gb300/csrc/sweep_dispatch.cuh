@@ -19,6 +19,11 @@ cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
+        // all of L1 that can be shared memory: the resident CTA count is set
+        // by the staging rings, not left to the driver's default split
+        e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR>, Cfg::NT,
                                                           Cfg::SMEM);
