@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 _SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2}
-_LIMITERS = {"none": 0, "minmod": 1, "mc": 2}
+_LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 _BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 
 _dp = C.POINTER(C.c_double)

@@ -32,7 +32,10 @@ extern "C" {
 #endif
 
 enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2 };
-enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_MC = 2 };
+/* ORC_LIM_NONE: unlimited second-order correction (Lax-Wendroff);
+ * ORC_LIM_FIRST_ORDER: no correction at all (Godunov's first-order upwind
+ * method: the Riemann solution and the fluctuation update alone). */
+enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_MC = 2, ORC_LIM_FIRST_ORDER = 3 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_EXTRAP = 1, ORC_BC_WALL = 2 };
 
 typedef struct {

@@ -6,7 +6,10 @@
  *     Q_i <- Q_i - nu (A+dQ_{i-1/2} + A-dQ_{i+1/2}) - nu (F_{i+1/2} - F_{i-1/2}),
  *     F_{i-1/2} = 1/2 sum_p |s_p| (1 - nu |s_p|) W~_p,
  * where W~_p is the wave limited against the same family's wave at the
- * upwind interface (Sec. 3, the wave limiter).  The x sweep maps Q^n to Q*,
+ * upwind interface (Sec. 3, the wave limiter).  Without the second term
+ * (W~ = 0) this is Godunov's first-order upwind method: the Riemann solution
+ * and its fluctuation update alone, the part of the sweep the paper isolates
+ * as its "Riemann solver" kernels (Sec. 7.1).  The x sweep maps Q^n to Q*,
  * the y sweep Q* to Q** (and z in 3D); every step runs x, y(, z) in order.
  * The CFL rule (Eq. CFL-condition, Sec. 4.1): a step taken with dt is kept
  * when dt * max_d(m_d / dx_d) <= cfl_max, else redone with the new estimate;
@@ -107,6 +110,7 @@ double orc_phi(int limiter, double theta)
         double a = theta < 1.0 ? theta : 1.0;
         return a > 0.0 ? a : 0.0;
     }
+    if (limiter == ORC_LIM_FIRST_ORDER) return 0.0;
     if (limiter == ORC_LIM_MC) {
         double a = 0.5 * (1.0 + theta);
         if (2.0 < a) a = 2.0;
@@ -199,8 +203,14 @@ static double update_line(const orc_problem *P, int d, double nu, line_work *w)
     }
 
     /* 2. Limiter at interfaces I = 0..N: compare each wave with the same
-     *    family's wave at the upwind interface (I-1 if s > 0, else I+1). */
+     *    family's wave at the upwind interface (I-1 if s > 0, else I+1).
+     *    The first-order method has no correction: W~ = 0, so F = 0. */
     for (int I = 0; I <= N; ++I) {
+        if (P->limiter == ORC_LIM_FIRST_ORDER) {
+            for (int p = 0; p < nw; ++p)
+                for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = 0.0;
+            continue;
+        }
         for (int p = 0; p < nw; ++p) {
             const double *Wi = w->W[I + 1][p];
             int J = w->s[I + 1][p] > 0.0 ? I - 1 : I + 1;

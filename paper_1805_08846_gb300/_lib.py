@@ -20,7 +20,7 @@ CLAW_OK, CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA, CLAW_ECFL, CLAW_ENONPHYS, CLAW_ET
 STATUS_NAMES = {0: "CLAW_OK", 1: "CLAW_EINVAL", 2: "CLAW_ENOMEM", 3: "CLAW_ECUDA", 4: "CLAW_ECFL",
                 5: "CLAW_ENONPHYS", 6: "CLAW_ETIMEOUT", 7: "CLAW_EBOUNDS"}
 SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2}
-LIMITERS = {"none": 0, "minmod": 1, "mc": 2}
+LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 
 

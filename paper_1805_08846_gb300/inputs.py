@@ -24,7 +24,7 @@ import numpy as np
 SEED = 1805
 
 SYSTEMS = ("acoustics", "acoustics_var", "shallow_water")
-LIMITERS = ("none", "minmod", "mc")
+LIMITERS = ("none", "minmod", "mc", "first_order")
 BCS = ("periodic", "extrap", "wall")
 
 

@@ -60,6 +60,9 @@ MUTANTS = [
      "        for (int d = P->ndim - 1; d >= 0; --d) {\n            m_d[d] = orc_sweep",
      "sweeps in y, x order"),
     ("orc_wavesweep.c", "    return 2 - d;", "    return 1 + d;", "transverse momentum mapped to the normal one"),
+    ("orc_wavesweep.c", "for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = 0.0;",
+     "for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = w->W[I + 1][p][c];",
+     "first-order method keeps the unlimited correction"),
 ]
 
 

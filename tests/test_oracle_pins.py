@@ -162,6 +162,7 @@ def test_limiter_table(theta, minmod, mc):
     assert oracle.phi("minmod", theta) == minmod
     assert oracle.phi("mc", theta) == mc
     assert oracle.phi("none", theta) == 1.0
+    assert oracle.phi("first_order", theta) == 0.0
 
 
 # ---------------------------------------------------------------- whole scheme
@@ -175,7 +176,7 @@ def right_going_acoustic(N, f, ny=2, rho=1.0, K=4.0, limiter="mc"):
     return line_problem("acoustics", N, ny=ny, limiter=limiter, q0=q0, rho=rho, K=K)
 
 
-@pytest.mark.parametrize("limiter", ["none", "minmod", "mc"])
+@pytest.mark.parametrize("limiter", ["none", "minmod", "mc", "first_order"])
 def test_exact_translation_at_courant_one(limiter):
     """At nu*c = 1 the correction vanishes and upwinding is an exact shift:
     a right-going wave moves one cell per step (any limiter)."""
@@ -253,6 +254,30 @@ def test_split_step_at_courant_one_is_composed_shifts():
     assert np.abs(xy - yx).max() > 0.1
 
 
+def test_first_order_step_is_characteristic_upwinding():
+    """Without the correction term a step of constant-coefficient acoustics
+    is upwinding of the two characteristic variables: w+ = (u + p/Z)/2 moves
+    right at c, w- = (u - p/Z)/2 left, so in one x sweep
+        w+_i <- w+_i - nu c (w+_i - w+_{i-1}),  w-_i <- w-_i + nu c (w-_{i+1} - w-_i),
+    and p = Z (w+ - w-), u = w+ + w-; v is untouched.  Random periodic data
+    on a y-uniform grid (the y sweep is then a no-op)."""
+    N, ny, rho, K = 50, 2, 1.0, 4.0
+    c, Z = math.sqrt(K / rho), math.sqrt(K * rho)
+    rng = np.random.default_rng(31)
+    row = rng.normal(size=(3, N))
+    q0 = np.repeat(row[:, None, :], ny, axis=1)
+    p = line_problem("acoustics", N, ny=ny, limiter="first_order", q0=q0, rho=rho, K=K)
+    nu_c = 0.6
+    r = Oracle(p).run_steps(q0, 1, fixed_dt=nu_c * p.dx[0] / c)["q"]
+    pr, u = row[0], row[1]
+    wp, wm = 0.5 * (u + pr / Z), 0.5 * (u - pr / Z)
+    wp1 = wp - nu_c * (wp - np.roll(wp, 1))
+    wm1 = wm + nu_c * (np.roll(wm, -1) - wm)
+    np.testing.assert_allclose(r[0][0], Z * (wp1 - wm1), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(r[1][0], wp1 + wm1, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(r[2][0], row[2])
+
+
 def plane_wave_error(N, limiter):
     f = lambda x: np.sin(2 * np.pi * x)
     p = right_going_acoustic(N, f, limiter=limiter)
@@ -269,6 +294,14 @@ def test_plane_wave_convergence(limiter, order):
     e = [plane_wave_error(N, limiter) for N in (64, 128, 256)]
     rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
     assert min(rates) >= order, (e, rates)
+
+
+def test_plane_wave_first_order_convergence():
+    """Without the correction term the method is first order: the error of
+    the smooth wave halves with the cell width (rate in [0.85, 1.2])."""
+    e = [plane_wave_error(N, "first_order") for N in (128, 256, 512)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert 0.85 <= min(rates) and max(rates) <= 1.2, (e, rates)
 
 
 def test_diagonal_plane_wave_converges():
@@ -384,7 +417,7 @@ def test_transonic_dam_break_entropy_fix():
 # ---------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("bc", ["periodic", "extrap", "wall"])
-@pytest.mark.parametrize("limiter", ["none", "minmod", "mc"])
+@pytest.mark.parametrize("limiter", ["none", "minmod", "mc", "first_order"])
 def test_lake_at_rest_bitwise(bc, limiter):
     """Constant depth and zero momentum stay exactly as they are."""
     q0 = np.zeros((3, 13, 17))
