@@ -190,6 +190,84 @@ def extra_acoustics3d(args, peak_gbs):
     return out
 
 
+# Sec. 7.1 (Tables 1-6): the paper's kernel-analysis problems.  Values a
+# sweep reads and writes per cell (fields it leaves unchanged are neither):
+# 2D acoustics p, u_d (2 + 2); shallow water h, hu, hv (3 + 3); 3D
+# variable-coefficient acoustics p, u_d (2 + 2) and Z, c (2 read).
+PAPER_PROBLEMS = (
+    ("acoustics_2d_1024", "mc", 4, "acoustics_2d_pulse", 1024),
+    ("shallow_water_1024", "minmod", 6, "sw_radial_dam_break", 1024),
+    ("acoustics_3d_96", "mc", 6, "acoustics_3d_layers", 96),
+)
+
+
+def paper_tables(args):
+    """Per-sweep times at the sizes of Sec. 7.1 Tables 1-6, for the full
+    method and for its first-order form (the Riemann solution and the
+    fluctuation update alone: the "Riemann solver" kernels of Tables 4-6),
+    FP32 and FP64.  DRAM bytes and flops per kernel come from ncu on the
+    same command (profiles/)."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    rows = []
+    for name, lim, vals, gen, n in PAPER_PROBLEMS:
+        for method in (lim, "first_order"):
+            prob = getattr(inputs, gen)(n, limiter=method)
+            for prec in (32, 64):
+                s = Solver.from_problem(prob, precision=prec)
+                if args.fixed_segments:
+                    for d in range(prob.ndim):
+                        s.set_segment(d, 64)
+                    seg = [64] * prob.ndim
+                else:
+                    seg = s.autotune(2)[:prob.ndim]
+                s.run_steps(args.warmup)
+                best = None
+                for _ in range(3 if not args.fixed_segments else 1):
+                    ms, tot, _nl = s.profile_steps(args.steps)
+                    if best is None or tot < best[1]:
+                        best = (ms, tot)
+                s.close()
+                ms, tot = best
+                es = prec // 8
+                alg = vals * es * prob.ncells
+                rows.append({
+                    "problem": name, "method": method, "precision": prec,
+                    "sweep_us": [round(1e3 * m, 2) for m in ms[:prob.ndim]],
+                    "step_us": round(1e3 * tot / args.steps, 2),
+                    "alg_bytes_per_sweep": alg,
+                    "achieved_gbs": [round(alg / (m * 1e-3) / 1e9, 1) for m in ms[:prob.ndim]],
+                    "cell_updates_per_s": prob.ncells * args.steps / (tot * 1e-3),
+                    "segments": seg})
+    print(json.dumps({"mode": "paper_tables", "steps": args.steps, "rows": rows}), flush=True)
+    return 0
+
+
+def size_scaling(args):
+    """Cell-updates/s against grid size, 256^2 .. 16384^2 (the paper's
+    problem-size scaling figures), both 2D systems, FP32 and FP64."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    rows = []
+    for name, gen in (("shallow_water", lambda n: inputs.sw_radial_dam_break(n)),
+                      ("acoustics_2d", lambda n: inputs.acoustics_2d_pulse(n))):
+        for n in (256, 512, 1024, 2048, 4096, 8192, 16384):
+            prob = gen(n)
+            for prec in (32, 64):
+                s = Solver.from_problem(prob, precision=prec)
+                seg = s.autotune(1 if n >= 8192 else 2)[:2]
+                cost = (1.0 if prec == 32 else 25.0) * prob.ncells   # ~cells x relative step cost
+                steps = int(max(3, min(200, 4e9 / cost)))
+                s.run_steps(3)
+                ms, tot, _nl = s.profile_steps(steps)
+                s.close()
+                rows.append({"system": name, "n": n, "precision": prec, "steps": steps,
+                             "ms_per_step": tot / steps,
+                             "cell_updates_per_s": prob.ncells * steps / (tot * 1e-3),
+                             "sweep_ms": ms[:2], "segments": seg})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "size_scaling", "rows": rows}), flush=True)
+    return 0
+
+
 def extra_ensembles(args):
     """Batched FP32 ensembles (one launch per sweep for all instances) against
     the plain FP64 path run instance by instance on the same instances."""
@@ -285,11 +363,27 @@ def main():
     ap.add_argument("--steps3", type=int, default=20)
     ap.add_argument("--segments", default=None,
                     help="fixed FP32 segment lengths 'x,y' instead of the autotuner's")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="per-sweep times at the sizes of the paper's kernel tables (one JSON line)")
+    ap.add_argument("--size-scaling", action="store_true",
+                    help="cell-updates/s from 256^2 to 16384^2 (one JSON line)")
+    ap.add_argument("--fixed-segments", action="store_true",
+                    help="with --paper-tables: 64-cell segments, no autotuning (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.paper_tables or args.size_scaling:
+        import torch
+        torch.cuda.set_device(0)
+        if args.paper_tables:
+            if "--steps" not in sys.argv:
+                args.steps = 20
+            paper_tables(args)
+        if args.size_scaling:
+            size_scaling(args)
+        return 0
 
     rank, world, local = dist_env()
     import torch

@@ -63,7 +63,17 @@ typedef enum {
 
 typedef enum { CLAW_BC_PERIODIC = 0, CLAW_BC_EXTRAP = 1, CLAW_BC_WALL = 2 } claw_bc;
 typedef enum { CLAW_ACOUSTICS = 0, CLAW_ACOUSTICS_VAR = 1, CLAW_SHALLOW_WATER = 2 } claw_system;
-typedef enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_MC = 2 } claw_limiter;
+/* Second-order correction of Sec. 3 Eq. LW-update: NONE applies it
+ * unlimited (Lax-Wendroff), MINMOD / MC limit each wave against its upwind
+ * neighbour; FIRST_ORDER drops it (Godunov's first-order upwind method: the
+ * Riemann solution and fluctuation update alone, the part of the sweep Sec.
+ * 7.1 measures as its "Riemann solver" kernels). */
+typedef enum {
+    CLAW_LIM_NONE = 0,
+    CLAW_LIM_MINMOD = 1,
+    CLAW_LIM_MC = 2,
+    CLAW_LIM_FIRST_ORDER = 3
+} claw_limiter;
 
 /* Grid of one problem: ndim = 2 or 3; n[d] interior cells (>= 2 in each
  * used direction; n[2] is ignored in 2D); dx[d] > 0 cell widths. */

@@ -419,7 +419,7 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
     if (!grids || !bc || !params) return fail(CLAW_EINVAL, "NULL argument");
     if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
-    if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_MC) return fail(CLAW_EINVAL, "unknown limiter %d", (int)limiter);
+    if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_FIRST_ORDER) return fail(CLAW_EINVAL, "unknown limiter %d", (int)limiter);
     const int ndim = grids[0].ndim;
     for (int i = 0; i < B; ++i) CKS(check_grid(&grids[i], ndim));
     if (system == CLAW_SHALLOW_WATER && ndim != 2) return fail(CLAW_EINVAL, "shallow water is 2D only");

@@ -317,7 +317,8 @@ struct ShallowWater {
 // the upwind wave's projection to the wave's own norm.  fmin/fmax return the
 // non-NaN operand, so a zero wave (theta = 0/0) still limits to zero.
 // ------------------------------------------------------------------------
-enum : int { kLimNone = 0, kLimMinmod = 1, kLimMC = 2 };
+// kLimFirstOrder: no correction term at all (first-order upwind)
+enum : int { kLimNone = 0, kLimMinmod = 1, kLimMC = 2, kLimFirstOrder = 3 };
 
 template <int LIM, class Real>
 __device__ __forceinline__ Real limiter_phi(Real theta) {

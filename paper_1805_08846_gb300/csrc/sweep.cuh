@@ -355,6 +355,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
     auto flux = [&](const V* d_up_left, const V* d_up_right, V* F) {
 #pragma unroll
         for (int c = 0; c < NQ; ++c) F[c] = V(0);
+        if (LIM == kLimFirstOrder) return;
 #pragma unroll
         for (int p = 0; p < NW; ++p) {
             const V sp = wB.s[p];
@@ -394,8 +395,12 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
 #pragma unroll
             for (int c = 0; c < NQ; ++c) {
                 const V first = apdqA[c] + wB.amdq[c];
-                const V second = F1[c] - F0[c];
-                qn[c] = vfma(nnu, second, vfma(nnu, first, qkeep[c]));
+                if (LIM == kLimFirstOrder) {
+                    qn[c] = vfma(nnu, first, qkeep[c]);
+                } else {
+                    const V second = F1[c] - F0[c];
+                    qn[c] = vfma(nnu, second, vfma(nnu, first, qkeep[c]));
+                }
             }
             if constexpr (Sys::kMinH) {
 #pragma unroll

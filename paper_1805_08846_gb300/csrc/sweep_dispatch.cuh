@@ -59,6 +59,7 @@ cudaError_t sweep_by_limiter(const SweepLaunch& L, const typename Sys::Params& P
     switch (L.limiter) {
         case kLimNone: return sweep_go<SysS, Real, kLimNone, DIR>(L, PS);
         case kLimMinmod: return sweep_go<SysS, Real, kLimMinmod, DIR>(L, PS);
+        case kLimFirstOrder: return sweep_go<SysS, Real, kLimFirstOrder, DIR>(L, PS);
         default: return sweep_go<SysS, Real, kLimMC, DIR>(L, PS);
     }
 }

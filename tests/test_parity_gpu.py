@@ -73,7 +73,11 @@ CASES += [("acoustics", (130, 67), "mc", ("wall", "extrap", "periodic", "wall"))
           ("shallow_water", (73, 20), "mc", "periodic"),
           ("acoustics", (129, 11), "minmod", "wall"),
           ("shallow_water", (2, 5), "minmod", "wall"),
-          ("acoustics_var", (3, 2, 2), "mc", "periodic")]
+          ("acoustics_var", (3, 2, 2), "mc", "periodic"),
+          # first-order method (no correction term)
+          ("acoustics", (37, 29), "first_order", "wall"),
+          ("shallow_water", (131, 67), "first_order", "extrap"),
+          ("acoustics_var", (23, 19, 21), "first_order", ("periodic", "periodic", "wall", "wall", "extrap", "extrap"))]
 
 
 @pytest.mark.parametrize("system,shape,limiter,bc", CASES)
