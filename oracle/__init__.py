@@ -21,6 +21,7 @@ from . import build as _build
 _SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2}
 _LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 _BCS = {"periodic": 0, "extrap": 1, "wall": 2}
+_SPLITTINGS = {"godunov": 0, "strang": 1}
 
 _dp = C.POINTER(C.c_double)
 
@@ -32,6 +33,7 @@ class _Problem(C.Structure):
         ("rho", C.c_double), ("K", C.c_double), ("g", C.c_double),
         ("cfl_desired", C.c_double), ("cfl_max", C.c_double), ("dt_max", C.c_double),
         ("max_retries", C.c_int), ("rho_cell", _dp), ("K_cell", _dp),
+        ("splitting", C.c_int),
     ]
 
 
@@ -93,6 +95,7 @@ class Oracle:
         P.cfl_desired, P.cfl_max = float(prob.cfl_desired), float(prob.cfl_max)
         P.dt_max = float(dt_max)
         P.max_retries = int(max_retries)
+        P.splitting = _SPLITTINGS[getattr(prob, "splitting", "godunov")]
         self._keep = []
         if prob.system == "acoustics_var":
             r = np.ascontiguousarray(prob.rho_cell, dtype=np.float64)

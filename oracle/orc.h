@@ -37,6 +37,10 @@ enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2 };
  * method: the Riemann solution and the fluctuation update alone). */
 enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_MC = 2, ORC_LIM_FIRST_ORDER = 3 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_EXTRAP = 1, ORC_BC_WALL = 2 };
+/* Sweep order of a step (the splittings of Eq. LW-update's Clawpack base,
+ * Sec. 3): GODUNOV x(dt) y(dt) [z(dt)]; STRANG x(dt/2) y(dt) x(dt/2) in 2D,
+ * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D. */
+enum { ORC_SPLIT_GODUNOV = 0, ORC_SPLIT_STRANG = 1 };
 
 typedef struct {
     int ndim;              /* 2 or 3 */
@@ -53,6 +57,7 @@ typedef struct {
     int max_retries;       /* consecutive rejections before giving up */
     const double *rho_cell;/* per-cell rho, K (ORC_ACOUSTICS_VAR), else NULL */
     const double *K_cell;
+    int splitting;         /* ORC_SPLIT_* */
 } orc_problem;
 
 /* Number of state fields m and waves mwaves for a problem. */
@@ -84,7 +89,13 @@ double orc_max_speed_dir(const orc_problem *P, int d, const double *q);
 /* Number of independent lines of direction d. */
 long orc_nlines(const orc_problem *P, int d);
 
+/* Sweeps of one step: direction and fraction of dt of each, in order;
+ * returns their number. */
+int orc_sequence(const orc_problem *P, int dirs[5], double frac[5]);
+
 /* Time stepping with the CFL rule (Eq. CFL-condition; Sec. 4.1 revert-and-redo).
+ * m_d is the largest speed over every sweep along d in the step; the
+ * Courant number of a step is dt * max_d(m_d / dx_d) for either splitting.
  *   mode 0: take nsteps accepted steps;  mode 1: advance to t_final.
  *   *dt <= 0 on entry: start from dt = cfl_desired / max_d(m_d / dx_d) of q.
  *   fixed_dt > 0: every step uses fixed_dt and is accepted (no CFL control).

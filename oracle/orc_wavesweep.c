@@ -347,6 +347,20 @@ static double next_dt(const orc_problem *P, double M)
     return dt < P->dt_max ? dt : P->dt_max;
 }
 
+int orc_sequence(const orc_problem *P, int dirs[5], double frac[5])
+{
+    int n = 0;
+    if (P->splitting == ORC_SPLIT_STRANG) {
+        /* half steps outside-in, the last direction a full step */
+        for (int d = 0; d < P->ndim - 1; ++d) { dirs[n] = d; frac[n] = 0.5; ++n; }
+        dirs[n] = P->ndim - 1; frac[n] = 1.0; ++n;
+        for (int d = P->ndim - 2; d >= 0; --d) { dirs[n] = d; frac[n] = 0.5; ++n; }
+    } else {
+        for (int d = 0; d < P->ndim; ++d) { dirs[n] = d; frac[n] = 1.0; ++n; }
+    }
+    return n;
+}
+
 int orc_run(const orc_problem *P, double *q, int mode, long nsteps, double t_final,
             double fixed_dt, double *t, double *dt, long *nacc, long *nrej,
             double *cfl_last)
@@ -379,8 +393,13 @@ int orc_run(const orc_problem *P, double *q, int mode, long nsteps, double t_fin
         double m_d[3] = {0.0, 0.0, 0.0};
         const double *src = q;
         double *dst = a;
-        for (int d = 0; d < P->ndim; ++d) {
-            m_d[d] = orc_sweep(P, d, src, dst, dt_try, 0, -1);
+        int dirs[5];
+        double frac[5];
+        int nsw = orc_sequence(P, dirs, frac);
+        for (int d = 0; d < 3; ++d) m_d[d] = 0.0;
+        for (int k = 0; k < nsw; ++k) {
+            double m = orc_sweep(P, dirs[k], src, dst, frac[k] * dt_try, 0, -1);
+            if (m > m_d[dirs[k]]) m_d[dirs[k]] = m;
             src = dst;
             dst = (dst == a) ? b : a;
         }

@@ -26,6 +26,7 @@ SEED = 1805
 SYSTEMS = ("acoustics", "acoustics_var", "shallow_water")
 LIMITERS = ("none", "minmod", "mc", "first_order")
 BCS = ("periodic", "extrap", "wall")
+SPLITTINGS = ("godunov", "strang")
 
 
 @dataclass
@@ -49,6 +50,7 @@ class Problem:
     rho_cell: Optional[np.ndarray] = None   # ([nz,] ny, nx) for acoustics_var
     K_cell: Optional[np.ndarray] = None
     name: str = ""
+    splitting: str = "godunov"    # one of SPLITTINGS
 
     @property
     def m(self) -> int:

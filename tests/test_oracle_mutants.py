@@ -63,6 +63,8 @@ MUTANTS = [
     ("orc_wavesweep.c", "for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = 0.0;",
      "for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = w->W[I + 1][p][c];",
      "first-order method keeps the unlimited correction"),
+    ("orc_wavesweep.c", "dirs[n] = P->ndim - 1; frac[n] = 1.0; ++n;",
+     "dirs[n] = P->ndim - 1; frac[n] = 0.5; ++n;", "Strang middle sweep takes half a step"),
 ]
 
 

@@ -224,6 +224,68 @@ def test_x_and_y_sweeps_agree_by_transposition():
     np.testing.assert_array_equal(rx[2], ry[1].T)
 
 
+def acoustic_sweep_exact(q, d, Z):
+    """One sweep of constant acoustics along d at Courant number 1: the
+    right-going characteristic variable (u_d + p/Z)/2 moves one cell forward,
+    the left-going one (u_d - p/Z)/2 one cell back; other velocities stay."""
+    pr, un = q[0], q[1 + d]
+    w_right = 0.5 * (un + pr / Z)
+    w_left = 0.5 * (un - pr / Z)
+    axis = q.ndim - 2 - d                 # x is the last array axis
+    w_right = np.roll(w_right, 1, axis=axis)
+    w_left = np.roll(w_left, -1, axis=axis)
+    out = q.copy()
+    out[0] = Z * (w_right - w_left)
+    out[1 + d] = w_right + w_left
+    return out
+
+
+def test_strang_step_is_symmetric_composition_of_shifts():
+    """Strang splitting x(dt/2) y(dt) x(dt/2): with dy = 2 dx and c dt = 2 dx
+    every sweep runs at Courant number 1 and is an exact characteristic
+    shift, so one step is shift_x . shift_y . shift_x (Godunov's x, y order
+    would give shift_y . shift_x over a full dt in x instead)."""
+    N, Z = 32, 2.0
+    rng = np.random.default_rng(41)
+    q0 = rng.normal(size=(3, N // 2, N))
+    p = inputs.Problem(2, (N, N // 2), (0, 0), (1, 1), "acoustics", "mc", ("periodic",) * 4, q0,
+                       K=4.0, splitting="strang")
+    assert p.dx[1] == 2 * p.dx[0]
+    r = Oracle(p).run_steps(q0, 1, fixed_dt=p.dx[0])["q"]        # c = 2
+    expect = acoustic_sweep_exact(acoustic_sweep_exact(acoustic_sweep_exact(q0, 0, Z), 1, Z), 0, Z)
+    np.testing.assert_allclose(r, expect, rtol=0, atol=1e-13)
+
+
+def test_strang_3d_step_is_symmetric_composition_of_shifts():
+    """3D Strang x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) with dz = 2 dx = 2 dy,
+    c dt = 2 dx: five exact shifts in that order."""
+    N, Z = 16, 2.0
+    rng = np.random.default_rng(43)
+    q0 = rng.normal(size=(4, N // 2, N, N))
+    p = inputs.Problem(3, (N, N, N // 2), (0, 0, 0), (1, 1, 1), "acoustics", "minmod", ("periodic",) * 6,
+                       q0, K=4.0, splitting="strang")
+    r = Oracle(p).run_steps(q0, 1, fixed_dt=p.dx[0])["q"]
+    e = q0
+    for d in (0, 1, 2, 1, 0):
+        e = acoustic_sweep_exact(e, d, Z)
+    np.testing.assert_allclose(r, e, rtol=0, atol=1e-13)
+
+
+def test_strang_on_y_uniform_data_is_two_half_steps():
+    """On y-uniform data the y sweep changes nothing, so a Strang step of dt
+    is x(dt/2) twice: bitwise the same as two Godunov steps of dt/2."""
+    N = 40
+    rng = np.random.default_rng(47)
+    row = np.stack([1.0 + 0.3 * rng.random(N), 0.2 * rng.normal(size=N), 0.1 * rng.normal(size=N)])
+    q0 = np.repeat(row[:, None, :], 3, axis=1)
+    pg = line_problem("shallow_water", N, ny=3, limiter="mc", q0=q0)
+    ps = pg.with_(splitting="strang")
+    dt = 0.4 * pg.dx[0] / 4.0
+    rs = Oracle(ps).run_steps(q0, 3, fixed_dt=dt)["q"]
+    rg = Oracle(pg).run_steps(q0, 6, fixed_dt=dt / 2)["q"]
+    np.testing.assert_array_equal(rs, rg)
+
+
 def test_split_step_at_courant_one_is_composed_shifts():
     """Constant acoustics with c dt = dx = dy: each sweep moves the
     right-going characteristic variable (u_d + p/Z)/2 one cell forward and
