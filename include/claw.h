@@ -79,16 +79,24 @@ typedef enum {
  * used direction; n[2] is ignored in 2D); dx[d] > 0 cell widths. */
 typedef struct { int ndim; int n[3]; double dx[3]; } claw_grid;
 
+/* Sweep order of a step.  GODUNOV: x(dt) y(dt) [z(dt)], Sec. 3 Eq.
+ * LW-update as the paper runs it.  STRANG: x(dt/2) y(dt) x(dt/2) in 2D,
+ * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D, the second-order splitting
+ * of the same Clawpack base.  Either way a step's Courant number is
+ * dt * max_d(m_d / dx_d), m_d the largest speed over the step's d sweeps. */
+typedef enum { CLAW_SPLIT_GODUNOV = 0, CLAW_SPLIT_STRANG = 1 } claw_splitting;
+
 /* rho, K: constant acoustics coefficients (also the initial per-cell values
  * of CLAW_ACOUSTICS_VAR); g: gravity; cfl_desired: Courant number the next
  * step aims at; cfl_max: a step above it is redone; dt_max: cap on dt;
  * precision: 32 or 64; max_retries: consecutive rejections before
- * CLAW_ECFL (<= 0 selects 8). */
+ * CLAW_ECFL (<= 0 selects 8); splitting: a claw_splitting. */
 typedef struct {
     double rho, K, g;
     double cfl_desired, cfl_max, dt_max;
     int precision;
     int max_retries;
+    int splitting;
 } claw_params;
 
 /* Ghost cells, two per side, filled inside each sweep from the state it is
@@ -219,8 +227,9 @@ claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system system,
 
 /* Take nsteps accepted steps like claw_run_steps inside one CUDA graph whose
  * kernels are bracketed by CUDA events, and report the average duration of
- * one launch of each kernel kind: kernel_ms[d] for the d-sweep (d < ndim),
- * kernel_ms[3] for the step-control kernel; *total_ms for the whole graph.
+ * one launch of each kernel kind: kernel_ms[d] for the d-sweep (d < ndim;
+ * with Strang splitting the sum over the step's d sweeps), kernel_ms[3]
+ * for the step-control kernel; *total_ms for the whole graph.
  * *launches receives the number of kernels launched.  Synchronises. */
 claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
                                double* total_ms, long* launches);

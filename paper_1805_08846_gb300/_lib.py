@@ -37,7 +37,7 @@ class claw_grid(C.Structure):
 class claw_params(C.Structure):
     _fields_ = [("rho", C.c_double), ("K", C.c_double), ("g", C.c_double),
                 ("cfl_desired", C.c_double), ("cfl_max", C.c_double), ("dt_max", C.c_double),
-                ("precision", C.c_int), ("max_retries", C.c_int)]
+                ("precision", C.c_int), ("max_retries", C.c_int), ("splitting", C.c_int)]
 
 
 _vp = C.c_void_p
@@ -131,10 +131,14 @@ def _stream_arg(stream):
     return C.c_void_p(int(stream))
 
 
+SPLITTINGS = {"godunov": 0, "strang": 1}
+
+
 def make_params(rho=1.0, K=1.0, g=9.81, cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, precision=64,
-                max_retries=8) -> claw_params:
+                max_retries=8, splitting="godunov") -> claw_params:
+    sp = SPLITTINGS[splitting] if isinstance(splitting, str) else int(splitting)
     return claw_params(float(rho), float(K), float(g), float(cfl_desired), float(cfl_max),
-                       float(dt_max), int(precision), int(max_retries))
+                       float(dt_max), int(precision), int(max_retries), sp)
 
 
 def make_grid(n, dx) -> claw_grid:

@@ -69,7 +69,7 @@ struct claw_solver {
     void* aux = nullptr;
     double* stage = nullptr;
     double* d_sums = nullptr;
-    int* d_counters = nullptr;          // persistent tile schedule, one per direction
+    int* d_counters = nullptr;          // persistent tile schedule, one per sweep of a step
     int* d_order[3] = {nullptr, nullptr, nullptr};
     bool persistent = true;
     size_t stage_elems = 0;
@@ -77,7 +77,11 @@ struct claw_solver {
     std::vector<TileDesc> tiles[3];
     TileDesc* d_tiles[3] = {nullptr, nullptr, nullptr};
     std::vector<std::pair<int, int>> inst_tiles[3];  // [lo, hi) tile range per instance
-    SlotMap slots[3]{};
+    // The step's sweeps in order: direction, fraction of dt, version slots.
+    int nseq = 0;
+    int seq_dir[kMaxSweeps]{};
+    double seq_frac[kMaxSweeps]{};
+    SlotMap seq_slots[kMaxSweeps]{};
     FinalSlots fin{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -164,12 +168,14 @@ claw_status build_tiles(claw_solver* s) {
     return CLAW_OK;
 }
 
-SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi) {
+// Arguments of a sweep along d; k is its place in the step's sequence (its
+// version slots and dt fraction), -1 for passes that update nothing.
+SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi, int k = -1) {
     SweepArgs a{};
     a.tiles = s->d_tiles[d] + tile_lo;
     const bool whole = tile_lo == 0 && tile_hi == (int)s->tiles[d].size();
     a.order = whole ? s->d_order[d] : nullptr;
-    a.tile_counter = s->d_counters + d;
+    a.tile_counter = s->d_counters + (k >= 0 ? k : 0);
     a.persistent = whole && s->persistent;
     a.ntiles = tile_hi - tile_lo;
     a.inst = s->d_inst;
@@ -180,16 +186,17 @@ SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi) {
     a.aux = s->aux;
     a.inst_lo = 0;
     a.inst_hi = s->B;
-    a.slots = s->slots[d];
+    if (k >= 0) a.slots = s->seq_slots[k];
+    a.dt_scale = k >= 0 ? s->seq_frac[k] : 1.0;
     a.Z = s->Z;
     a.c = s->c;
     a.g = s->params.g;
     return a;
 }
 
-claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, bool speeds) {
+claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, bool speeds, int k = -1) {
     SweepLaunch L{};
-    L.args = sweep_args(s, d, tile_lo, tile_hi);
+    L.args = sweep_args(s, d, tile_lo, tile_hi, k);
     L.system = s->system;
     L.limiter = s->limiter;
     L.dir = d;
@@ -229,10 +236,16 @@ long long tiles_for_segment(const claw_solver* s, int d, int L) {
     return t;
 }
 
-// One step attempt for every instance: the sweeps in x, y(, z) order, then
-// the step-control kernel.
+// Sweep k of the step's sequence over every tile of its direction.
+claw_status launch_seq_sweep(claw_solver* s, int k) {
+    const int d = s->seq_dir[k];
+    return launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false, k);
+}
+
+// One step attempt for every instance: the step's sweeps in order, then the
+// step-control kernel.
 claw_status enqueue_attempt(claw_solver* s) {
-    for (int d = 0; d < s->ndim; ++d) CKS(launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false));
+    for (int k = 0; k < s->nseq; ++k) CKS(launch_seq_sweep(s, k));
     CK(launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->d_counters, s->stream));
     return CLAW_OK;
 }
@@ -430,6 +443,8 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     for (int k = 0; k < 2 * ndim; ++k)
         if (bc[k] < CLAW_BC_PERIODIC || bc[k] > CLAW_BC_WALL) return fail(CLAW_EINVAL, "unknown bc[%d] = %d", k, (int)bc[k]);
     if (params->precision != 32 && params->precision != 64) return fail(CLAW_EINVAL, "precision must be 32 or 64");
+    if (params->splitting != CLAW_SPLIT_GODUNOV && params->splitting != CLAW_SPLIT_STRANG)
+        return fail(CLAW_EINVAL, "unknown splitting %d", params->splitting);
     if (!(params->cfl_desired > 0.0) || !(params->cfl_max > 0.0)) return fail(CLAW_EINVAL, "cfl_desired and cfl_max must be > 0");
     if (!(params->dt_max > 0.0)) return fail(CLAW_EINVAL, "dt_max must be > 0");
     if (system != CLAW_SHALLOW_WATER && (!(params->rho > 0.0) || !(params->K > 0.0)))
@@ -497,8 +512,8 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     s->stage_elems = max_cells * m;
     CK(cudaMalloc(&s->stage, s->stage_elems * sizeof(double)));
     CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
-    CK(cudaMalloc(&s->d_counters, 4 * sizeof(int)));
-    CK(cudaMemsetAsync(s->d_counters, 0, 4 * sizeof(int), s->stream));
+    CK(cudaMalloc(&s->d_counters, kMaxSweeps * sizeof(int)));
+    CK(cudaMemsetAsync(s->d_counters, 0, kMaxSweeps * sizeof(int), s->stream));
     CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
     CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
     {
@@ -522,14 +537,25 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     CK(cudaMemcpyAsync(s->d_ctl, ctl.data(), sizeof(Control) * B, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMallocHost(&s->h_ctl, sizeof(Control) * B));
 
-    // Version slots: each sweep reads a field's latest version of the step
-    // and writes the next one; a field's versions cycle through 3 slots.
+    // The step's sweep sequence (Godunov x, y(, z); Strang half steps
+    // outside-in around a full step in the last direction) and each sweep's
+    // version slots: a sweep reads a field's latest version of the step and
+    // writes the next one; versions after Q^n alternate between slots 1 and
+    // 2, so Q^n stays intact until the step is accepted.
+    s->nseq = 0;
+    if (params->splitting == CLAW_SPLIT_STRANG) {
+        for (int d = 0; d < ndim - 1; ++d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 0.5; }
+        s->seq_dir[s->nseq] = ndim - 1; s->seq_frac[s->nseq++] = 1.0;
+        for (int d = ndim - 2; d >= 0; --d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 0.5; }
+    } else {
+        for (int d = 0; d < ndim; ++d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 1.0; }
+    }
     int ver[4] = {0, 0, 0, 0};
-    for (int d = 0; d < ndim; ++d) {
-        memset(&s->slots[d], 0, sizeof(SlotMap));
-        for (int f : touched_fields(system, d)) {
-            s->slots[d].in_off[f] = (signed char)slot_of_version(ver[f]);
-            s->slots[d].out_off[f] = (signed char)slot_of_version(ver[f] + 1);
+    for (int k = 0; k < s->nseq; ++k) {
+        memset(&s->seq_slots[k], 0, sizeof(SlotMap));
+        for (int f : touched_fields(system, s->seq_dir[k])) {
+            s->seq_slots[k].in_off[f] = (signed char)slot_of_version(ver[f]);
+            s->seq_slots[k].out_off[f] = (signed char)slot_of_version(ver[f] + 1);
             ver[f] += 1;
         }
     }
@@ -855,7 +881,7 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
                                long* launches) {
     CKS(check_solver(s));
     if (nsteps < 1) return fail(CLAW_EINVAL, "nsteps must be >= 1");
-    const int nk = s->ndim + 1;
+    const int nk = s->nseq + 1;
     std::vector<cudaEvent_t> ev((size_t)nsteps * nk * 2);
     for (auto& e : ev) CK(cudaEventCreate(&e));
     cudaEvent_t t0, t1;
@@ -866,12 +892,12 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     claw_status st = CLAW_OK;
     for (int k = 0; k < nsteps && st == CLAW_OK; ++k) {
-        for (int d = 0; d <= s->ndim && st == CLAW_OK; ++d) {
-            cudaEvent_t* e = &ev[((size_t)k * nk + d) * 2];
+        for (int j = 0; j <= s->nseq && st == CLAW_OK; ++j) {
+            cudaEvent_t* e = &ev[((size_t)k * nk + j) * 2];
             // External records become event nodes of the graph (timestamps),
             // not just capture dependencies.
             cudaEventRecordWithFlags(e[0], s->stream, cudaEventRecordExternal);
-            if (d < s->ndim) st = launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false);
+            if (j < s->nseq) st = launch_seq_sweep(s, j);
             else if (launch_finish(s->d_ctl, s->d_inst, 0, s->B, s->fin, s->d_counters, s->stream) != cudaSuccess)
                 st = fail(CLAW_ECUDA, "finish launch failed");
             cudaEventRecordWithFlags(e[1], s->stream, cudaEventRecordExternal);
@@ -889,11 +915,11 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4], 
     CK(cudaStreamSynchronize(s->stream));
     double acc[4] = {0, 0, 0, 0};
     for (int k = 0; k < nsteps; ++k)
-        for (int d = 0; d <= s->ndim; ++d) {
+        for (int j = 0; j <= s->nseq; ++j) {
             float ms = 0.f;
-            cudaEvent_t* e = &ev[((size_t)k * nk + d) * 2];
+            cudaEvent_t* e = &ev[((size_t)k * nk + j) * 2];
             CK(cudaEventElapsedTime(&ms, e[0], e[1]));
-            acc[d < s->ndim ? d : 3] += ms;
+            acc[j < s->nseq ? s->seq_dir[j] : 3] += ms;
         }
     float tot = 0.f;
     CK(cudaEventElapsedTime(&tot, t0, t1));

@@ -9,6 +9,9 @@ namespace claw {
 
 // Threads (one grid line each) per tile / CTA of a sweep.
 constexpr int kLines = 128;
+// sweeps per step at most (3D Strang: x y z y x); each has its own
+// persistent tile counter
+constexpr int kMaxSweeps = 5;
 
 // Status bits latched on the device and reported by synchronising calls.
 enum : unsigned {
@@ -104,6 +107,7 @@ struct SweepArgs {
     int ntiles;
     int inst_lo, inst_hi;  // instances this launch may touch
     SlotMap slots;
+    double dt_scale;   // this sweep's fraction of the step's dt (Strang: 1/2 or 1)
     int m;                 // fields per state version (TMA plane = slot * m + field)
     double Z, c, g;        // constant acoustics impedance / speed; gravity
 };

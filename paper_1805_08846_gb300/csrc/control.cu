@@ -47,7 +47,8 @@ __device__ __forceinline__ void prepare_attempt(Control& c) {
 __global__ void arm_kernel(Control* ctl, int lo, int hi, int mode, long long nsteps,
                            double t_final, double fixed_dt, double cfl_desired, int* counters) {
     const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == lo && counters) counters[0] = counters[1] = counters[2] = 0;
+    if (i == lo && counters)
+        for (int k = 0; k < kMaxSweeps; ++k) counters[k] = 0;
     if (i >= hi) return;
     Control& c = ctl[i];
     if (cfl_desired > 0.0 && cfl_desired != c.cfl_desired) {
@@ -68,7 +69,8 @@ __global__ void finish_kernel(Control* ctl, const InstDesc* inst, int lo, int hi
                               int* counters) {
     const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
     // the sweeps of this attempt are done: rewind their tile schedules
-    if (i == lo && counters) counters[0] = counters[1] = counters[2] = 0;
+    if (i == lo && counters)
+        for (int k = 0; k < kMaxSweeps; ++k) counters[k] = 0;
     if (i >= hi) return;
     Control& c = ctl[i];
     if (!c.active) return;

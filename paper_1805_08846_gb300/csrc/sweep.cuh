@@ -323,7 +323,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
         Sys::prepare(cell, P);
     };
 
-    const Real nu_s = (Real)(ctl->dt_attempt / I.dx[DIR]);
+    const Real nu_s = (Real)(ctl->dt_attempt * A.dt_scale / I.dx[DIR]);
     const V nu = V(nu_s), nnu = V(-nu_s);
     SM smax = 0;
     bool bad = false;

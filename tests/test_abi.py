@@ -57,6 +57,7 @@ def _create(**over):
     (dict(params=L.make_params(precision=16)), "precision"),
     (dict(params=L.make_params(cfl_desired=0.0)), "cfl_desired"),
     (dict(params=L.make_params(g=-1.0)), "g must be"),
+    (dict(params=L.make_params(splitting=7)), "unknown splitting"),
     (dict(system="acoustics", m=3, mwaves=2, params=L.make_params(rho=0.0)), "rho and K"),
     (dict(system=7), "unknown system"),
     (dict(limiter=9), "unknown limiter"),

@@ -56,8 +56,8 @@ MUTANTS = [
      "MC centred slope without the 1/2"),
     ("orc_wavesweep.c", "double dt = M > 0.0 ? P->cfl_desired / M : P->dt_max;",
      "double dt = M > 0.0 ? P->cfl_max / M : P->dt_max;", "next step at cfl_max"),
-    ("orc_wavesweep.c", "        for (int d = 0; d < P->ndim; ++d) {\n            m_d[d] = orc_sweep",
-     "        for (int d = P->ndim - 1; d >= 0; --d) {\n            m_d[d] = orc_sweep",
+    ("orc_wavesweep.c", "for (int d = 0; d < P->ndim; ++d) { dirs[n] = d; frac[n] = 1.0; ++n; }",
+     "for (int d = P->ndim - 1; d >= 0; --d) { dirs[n] = d; frac[n] = 1.0; ++n; }",
      "sweeps in y, x order"),
     ("orc_wavesweep.c", "    return 2 - d;", "    return 1 + d;", "transverse momentum mapped to the normal one"),
     ("orc_wavesweep.c", "for (int c = 0; c < nq; ++c) w->Wt[I + 1][p][c] = 0.0;",

@@ -274,6 +274,42 @@ def test_t_final_in_the_past_is_rejected():
         assert ei.value.status == L.CLAW_EINVAL
 
 
+# ------------------------------------------------------------ Strang splitting
+
+STRANG_CASES = [("shallow_water", (45, 38), "minmod", "periodic"),
+                ("shallow_water", (64, 33), "mc", ("extrap", "wall", "wall", "extrap")),
+                ("acoustics", (37, 29), "mc", "wall"),
+                ("acoustics_var", (23, 19, 21), "mc", ("periodic", "periodic", "wall", "wall", "extrap", "extrap")),
+                ("acoustics", (17, 21, 25), "first_order", "periodic")]
+
+
+@pytest.mark.parametrize("system,shape,limiter,bc", STRANG_CASES)
+@pytest.mark.parametrize("precision", [64, 32])
+def test_strang_splitting_matches_oracle(system, shape, limiter, bc, precision):
+    """x(dt/2) y(dt) x(dt/2) (3D: x y z(dt) y x): each sweep's dt fraction
+    and version slots, the per-direction speed maximum over the step."""
+    prob = inputs.random_problem(system, shape, limiter, bc, discontinuous=True).with_(splitting="strang")
+    q, (t, dt, n), ref = run_both(prob, 10, precision)
+    assert n == 10
+    if precision == 64:
+        assert fieldwise_linf(q, ref["q"]) <= TOL64
+        assert t == pytest.approx(ref["t"], rel=1e-13)
+    else:
+        check_fp32(prob, q, ref["q"])
+        assert t == pytest.approx(ref["t"], rel=1e-5)
+
+
+def test_strang_ensemble_matches_oracle_per_instance():
+    probs = [p.with_(splitting="strang") for p in inputs.sw_ensemble(B=5, nmin=16, nmax=70, nsteps=8)]
+    e = Ensemble.from_problems(probs, precision=64)
+    e.run_steps(8)
+    for i, p in enumerate(probs):
+        ref = Oracle(p).run_steps(p.q0, 8)
+        assert fieldwise_linf(e.get_q(i), ref["q"]) <= TOL64
+        assert e.time(i)[0] == pytest.approx(ref["t"], rel=1e-14)
+    e.close()
+
+
 # ------------------------------------------------------------------ ensembles
 
 def test_small_sw_ensemble_matches_oracle_per_instance():
