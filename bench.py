@@ -408,7 +408,7 @@ def main():
             for d, L_ in enumerate(segs[precision]):
                 s.set_segment(d, L_)
         else:
-            segs[precision] = s.autotune(2)           # tile shapes (state restored)
+            segs[precision] = s.autotune(4)           # tile shapes (state restored)
         s.run_steps(args.warmup)                      # warm-up: graphs, caches, clocks
         barrier(world)
         torch.cuda.synchronize()

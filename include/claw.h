@@ -246,7 +246,7 @@ claw_status claw_probe_fma(int precision, double* flops_per_s, void* cuda_stream
 claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 
 /* Autotuner: for every direction, time trial_steps steps (CUDA events around
- * each sweep) with each candidate segment length and keep the fastest.  The
+ * each sweep) twice with each candidate segment length and keep the fastest.  The
  * candidates are fixed lengths plus, for w = 1..4, the shortest length whose
  * tiles fit in w waves of the CTAs the GPU holds at once;
  * seg_out[d] (may be NULL) receives the choice.  The state, clock and step
