@@ -248,7 +248,9 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 /* Autotuner: for every direction, time trial_steps steps (CUDA events around
  * each sweep) twice with each candidate segment length and keep the fastest.  The
  * candidates are fixed lengths plus, for w = 1..4, the shortest length whose
- * tiles fit in w waves of the CTAs the GPU holds at once;
+ * tiles fit in w waves of the CTAs the GPU holds at once; a second pass
+ * tries the lengths that split the longest line into equal whole chunks
+ * within a factor 1.5 of the first pass's best;
  * seg_out[d] (may be NULL) receives the choice.  The state, clock and step
  * counters are restored afterwards, so the solution is unchanged.
  * Synchronises. */

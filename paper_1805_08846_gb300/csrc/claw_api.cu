@@ -74,6 +74,7 @@ struct claw_solver {
     bool persistent = true;
     size_t stage_elems = 0;
     int seg[3] = {64, 64, 64};
+    int tile_lines[3] = {kLines, kLines, kLines};   // lines per tile, from the sweep kernels
     std::vector<TileDesc> tiles[3];
     TileDesc* d_tiles[3] = {nullptr, nullptr, nullptr};
     std::vector<std::pair<int, int>> inst_tiles[3];  // [lo, hi) tile range per instance
@@ -135,12 +136,12 @@ claw_status build_tiles(claw_solver* s) {
             }
             if (d == 0) {
                 const int rows = I.n[1] * I.n[2];
-                for (int r0 = 0; r0 < rows; r0 += kLines)
+                for (int r0 = 0; r0 < rows; r0 += s->tile_lines[0])
                     for (auto& sg : segs) T.push_back({i, r0, 0, sg.first, sg.second, {0, 0, 0}});
             } else {
                 const int others = (d == 1) ? I.n[2] : I.n[1];
                 for (int o = 0; o < others; ++o)
-                    for (int x0 = 0; x0 < I.n[0]; x0 += kLines)
+                    for (int x0 = 0; x0 < I.n[0]; x0 += s->tile_lines[d])
                         for (auto& sg : segs) T.push_back({i, x0, o, sg.first, sg.second, {0, 0, 0}});
             }
             s->inst_tiles[d][i] = {lo, (int)T.size()};
@@ -156,7 +157,7 @@ claw_status build_tiles(claw_solver* s) {
         auto cells = [&](const TileDesc& td) {
             const InstDesc& I = s->inst[td.inst];
             const int nl = d == 0 ? I.n[1] * I.n[2] : I.n[0];
-            return (long long)std::min(kLines, nl - td.line0) * (td.b - td.a);
+            return (long long)std::min(s->tile_lines[d], nl - td.line0) * (td.b - td.a);
         };
         std::stable_sort(order.begin(), order.end(),
                          [&](int x, int y) { return cells(T[x]) > cells(T[y]); });
@@ -188,6 +189,7 @@ SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi, int k = -1
     a.inst_hi = s->B;
     if (k >= 0) a.slots = s->seq_slots[k];
     a.dt_scale = k >= 0 ? s->seq_frac[k] : 1.0;
+    a.lines = s->tile_lines[d];
     a.Z = s->Z;
     a.c = s->c;
     a.g = s->params.g;
@@ -229,8 +231,9 @@ long long tiles_for_segment(const claw_solver* s, int d, int L) {
     long long t = 0;
     for (int i = 0; i < s->B; ++i) {
         const InstDesc& I = s->inst[i];
-        const long long groups = d == 0 ? ((long long)I.n[1] * I.n[2] + kLines - 1) / kLines
-                                        : (long long)(d == 1 ? I.n[2] : I.n[1]) * ((I.n[0] + kLines - 1) / kLines);
+        const int tl = s->tile_lines[d];
+        const long long groups = d == 0 ? ((long long)I.n[1] * I.n[2] + tl - 1) / tl
+                                        : (long long)(d == 1 ? I.n[2] : I.n[1]) * ((I.n[0] + tl - 1) / tl);
         t += groups * ((I.n[d] + L - 1) / L);
     }
     return t;
@@ -371,7 +374,8 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
     const InstDesc& I = s->inst[i];
     const CUtensorMapDataType dt = s->precision == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t es = s->esize;
-    // x sweep boxes: the kernel's chunk of each row (32 bytes: swizzled)
+    // x sweep boxes: the kernel's chunk of each row (32 bytes: swizzled) ×
+    // its lines per tile; y / z boxes: lines per tile adjacent x × a chunk
     int chunk = 0;
     {
         SweepLaunch L{};
@@ -384,6 +388,8 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
         CK(launch_sweep(L));
     }
     const cuuint32_t cx = (cuuint32_t)chunk;
+    const cuuint32_t lx = (cuuint32_t)s->tile_lines[0], ly = (cuuint32_t)s->tile_lines[1],
+                     lz = (cuuint32_t)s->tile_lines[2];
     const CUtensorMapSwizzle xsw = cx * es == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
     const cuuint32_t ct = (cuuint32_t)(32 / es);   // cells per chunk along y / z (4 KB boxes)
     for (int kind = 0; kind < 2; ++kind) {
@@ -393,7 +399,7 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
         {
             const cuuint64_t dims[3] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1] * I.n[2], planes};
             const cuuint64_t str[2] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.fstride * es};
-            const cuuint32_t box[3] = {cx, (cuuint32_t)kLines, 1};
+            const cuuint32_t box[3] = {cx, lx, 1};
             // L2 promotion of 128 B: 256 B fetches whole neighbouring
             // segments' blocks that are evicted before those segments reach
             // them (measured: 1.24x the algorithmic bytes vs 1.03x, and the
@@ -404,11 +410,11 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
         const cuuint64_t str[3] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.n[1] * I.pitch * es,
                                    (cuuint64_t)I.fstride * es};
         {
-            const cuuint32_t box[4] = {(cuuint32_t)kLines, ct, 1, 1};
+            const cuuint32_t box[4] = {ly, ct, 1, 1};
             CKS(encode(&T.map[3 * kind + 1], dt, 4, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE));
         }
         if (s->ndim == 3) {
-            const cuuint32_t box[4] = {(cuuint32_t)kLines, 1, ct, 1};
+            const cuuint32_t box[4] = {lz, 1, ct, 1};
             CKS(encode(&T.map[3 * kind + 2], dt, 4, base, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE));
         }
     }
@@ -516,6 +522,18 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     CK(cudaMemsetAsync(s->d_counters, 0, kMaxSweeps * sizeof(int), s->stream));
     CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
     CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
+    // Lines per tile of each direction's sweep kernel (tile lists and
+    // bulk-tensor boxes follow it).
+    for (int d = 0; d < ndim; ++d) {
+        SweepLaunch L{};
+        L.system = s->system;
+        L.limiter = s->limiter;
+        L.dir = d;
+        L.precision = s->precision;
+        L.grid = 1;
+        L.lines_out = &s->tile_lines[d];
+        CK(launch_sweep(L));
+    }
     {
         std::vector<TmaSet> tma(B);
         for (int i = 0; i < B; ++i) CKS(encode_instance(s, i, tma[i]));
@@ -853,22 +871,38 @@ claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
         std::sort(cand.begin(), cand.end());
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
         double best_ms = 1e30;
-        for (size_t k = 0; k < cand.size() && st == CLAW_OK; ++k) {
-            if (cand[k] > 2 * maxN && k > 0) break;
-            st = claw_set_segment(s, d, cand[k]);
-            if (st != CLAW_OK) break;
+        std::vector<int> tried;
+        auto trial = [&](int L) -> claw_status {
+            if (std::find(tried.begin(), tried.end(), L) != tried.end()) return CLAW_OK;
+            tried.push_back(L);
+            CKS(claw_set_segment(s, d, L));
             // best of two trials from the same state (the first also warms
             // caches and the new tile lists)
-            for (int rep = 0; rep < 2 && st == CLAW_OK; ++rep) {
+            for (int rep = 0; rep < 2; ++rep) {
                 double ms[4], tot;
                 long nl;
-                st = claw_profile_steps(s, trial_steps, ms, &tot, &nl);
-                if (st == CLAW_OK && ms[d] < best_ms) {
+                CKS(claw_profile_steps(s, trial_steps, ms, &tot, &nl));
+                if (ms[d] < best_ms) {
                     best_ms = ms[d];
                     best[d] = s->seg[d];
                 }
-                if (st == CLAW_OK) st = restore();
+                CKS(restore());
             }
+            return CLAW_OK;
+        };
+        for (size_t k = 0; k < cand.size() && st == CLAW_OK; ++k) {
+            if (cand[k] > 2 * maxN && k > 0) break;
+            st = trial(cand[k]);
+        }
+        // Second pass: lengths that split the longest line into equal whole
+        // chunks (k segments, no short tail), within a factor 1.5 of the
+        // first pass's best.
+        const int b0 = best[d];
+        for (int k = 1; k <= 256 && st == CLAW_OK; ++k) {
+            const int L = ((maxN + k - 1) / k + 7) / 8 * 8;
+            if (L < 8) break;
+            if (2 * L > 3 * b0 || 3 * L < 2 * b0) continue;
+            st = trial(L);
         }
         if (st == CLAW_OK) st = claw_set_segment(s, d, best[d]);
     }

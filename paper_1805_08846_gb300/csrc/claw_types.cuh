@@ -108,6 +108,7 @@ struct SweepArgs {
     int inst_lo, inst_hi;  // instances this launch may touch
     SlotMap slots;
     double dt_scale;   // this sweep's fraction of the step's dt (Strang: 1/2 or 1)
+    int lines;         // lines per tile of this direction's tile list
     int m;                 // fields per state version (TMA plane = slot * m + field)
     double Z, c, g;        // constant acoustics impedance / speed; gravity
 };

@@ -18,6 +18,7 @@ struct SweepLaunch {
     cudaStream_t stream;
     int* resident_out;   // non-null: report the CTAs the GPU holds at once, launch nothing
     int* chunk_out;      // non-null: report the cells per staged chunk, launch nothing
+    int* lines_out;      // non-null: report the lines per tile, launch nothing
 };
 
 // Record the thread-local message claw_last_error() returns.

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
     const InstDesc& I = A.inst[td.inst];
     Control* ctl = A.ctl + td.inst;
     long long base, stride;
-    const bool valid = line_geometry<DIR>(td, I, threadIdx.x, base, stride);
+    const bool valid = line_geometry<DIR>(td, I, threadIdx.x, base, stride) && (int)threadIdx.x < A.lines;
     const int N = I.n[DIR];
     const int bc_lo = I.bc[2 * DIR], bc_hi = I.bc[2 * DIR + 1];
     const Real* pool = static_cast<const Real*>(A.pool);
@@ -181,11 +181,14 @@ template <class Sys, class Real, int DIR>
 struct StageCfg {
     // lines per thread: 2 when the system computes on f2 (two FP32 lines)
     static constexpr int PK = Lanes<typename Sys::Value>::N;
-    static constexpr int NT = kLines / PK;                      // threads per CTA
+    // lines per tile: 128, or 64 for the two-line x sweep (one-warp CTAs
+    // whose three-stage ring is small enough for 11 CTAs per SM)
+    static constexpr int LINES = (PK == 2 && DIR == 0) ? kLines / 2 : kLines;
+    static constexpr int NT = LINES / PK;                       // threads per CTA
     static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
     static constexpr int G = 16 / (int)sizeof(Real);            // cells per 16-byte half
-    static constexpr int BOX = kLines * C * (int)sizeof(Real);   // bytes per plane box
+    static constexpr int BOX = LINES * C * (int)sizeof(Real);    // bytes per plane box
     // y, z: two stages suffice for the two-line form (more CTAs fit); the x
     // sweep refills a stage only after the write-back of the chunk before
     // has read it, which needs three
@@ -199,7 +202,7 @@ struct StageCfg {
     // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
     // a 5-CTA budget forces worse schedules), 2 for FP64; 6 CTAs of 64
     // two-line threads for the packed form (7 fit at run time)
-    static constexpr int MIN_CTAS = PK == 2 ? 6 : (sizeof(Real) == 4 ? 4 : 2);
+    static constexpr int MIN_CTAS = PK == 2 ? (DIR == 0 ? 12 : 6) : (sizeof(Real) == 4 ? 4 : 2);
 };
 
 template <class Sys, class Real, int LIM, int DIR>
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
     // (the 32-byte swizzle of row r swaps its halves on bit 2 of r)
     auto pos_off = [&](int line, int jj) {
         return DIR == 0 ? line * 32 + 16 * ((jj / G) ^ ((line >> 2) & 1)) + (jj % G) * (int)sizeof(Real)
-                        : (jj * kLines + line) * (int)sizeof(Real);
+                        : (jj * Cfg::LINES + line) * (int)sizeof(Real);
     };
     auto stage_of = [&](int kk) { return smem + ((kbase + kk) % STAGES) * Cfg::STAGE_BYTES; };
     auto put_stage = [&](int i, const V* qn) {

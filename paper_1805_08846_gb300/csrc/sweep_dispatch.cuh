@@ -10,8 +10,9 @@ template <class Sys, class Real, int LIM, int DIR>
 cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     if (L.grid == 0) return cudaSuccess;
     using Cfg = StageCfg<Sys, Real, DIR>;
-    if (L.chunk_out) {
-        *L.chunk_out = Cfg::C;
+    if (L.chunk_out || L.lines_out) {
+        if (L.chunk_out) *L.chunk_out = Cfg::C;
+        if (L.lines_out) *L.lines_out = Cfg::LINES;
         return cudaSuccess;
     }
     static int resident = 0;   // CTAs of this kernel the whole GPU holds at once

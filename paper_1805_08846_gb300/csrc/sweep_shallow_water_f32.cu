@@ -1,8 +1,6 @@
-// Sweep kernels: shallow water (Roe + Harten-Hyman), float, 2D only.  The y
-// sweep marches two lines per thread on packed FP32 pairs (f2).  The x sweep
-// stays scalar: its results return through a three-stage ring that leaves
-// room for too few two-line CTAs per SM (measured slower both with 32-byte
-// and with 16-byte rows); so does the speeds-only pass.
+// Sweep kernels: shallow water (Roe + Harten-Hyman), float, 2D only.  The
+// sweeps march two lines per thread on packed FP32 pairs (f2); the
+// speeds-only pass stays scalar.
 #include <math.h>
 
 #include "sweep_dispatch.cuh"
@@ -14,6 +12,6 @@ cudaError_t launch_sweep_shallow_water_f32(const SweepLaunch& L) {
     const float g = (float)L.args.g, sg = (float)sqrt(L.args.g), hg = (float)(0.5 * L.args.g);
     const S::Params P{g, sg, hg};
     const S2::Params P2{f2(g), f2(sg), f2(hg)};
-    return sweep_by_dir<S, float, false, S, S2>(L, P, P, P2);
+    return sweep_by_dir<S, float, false, S2, S2>(L, P, P2, P2);
 }
 }  // namespace claw
