@@ -548,7 +548,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
         // One cell of line `lane` at a time.  x sweep: the result of cell
         // a + k*C + j - 2 overwrites an input position of this or the previous
         // chunk that has already been consumed.
-#pragma unroll 2
+#pragma unroll 4   // measured: 2 -> 4 takes 3% off the x sweep, 8 is slower
         for (int j = jlo; j < jhi; ++j) {
             V vals[NP];
             if constexpr (PK == 2 && DIR != 0) {
