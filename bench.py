@@ -268,6 +268,108 @@ def size_scaling(args):
     return 0
 
 
+def accuracy(args):
+    """Errors of the GPU paths on the five workloads, against the FP64 oracle
+    (or, for the 3D acoustics ensemble and 100 steps of the 512^3 problem,
+    against the FP64 GPU path pinned to it), with the time of each path:
+    relative L-inf per field (worst field) for FP64, relative L1 on h and on
+    h - 1 for FP32 shallow water, relative L2 (worst field) for FP32
+    acoustics.  The oracle runs on all host cores."""
+    import oracle as orc
+    from oracle import Oracle
+    from paper_1805_08846_gb300 import Ensemble, Solver, inputs
+
+    def linf(a, b):
+        return max(orc.rel_linf(a[f], b[f]) for f in range(a.shape[0]))
+
+    def l2(a, b):
+        return max(orc.rel_l2(a[f], b[f]) for f in range(a.shape[0]) if np.abs(b[f]).max() > 0)
+
+    def gpu(prob, steps, prec):
+        with Solver.from_problem(prob, precision=prec) as s:
+            s.autotune(2)
+            t0 = time.perf_counter()
+            s.run_steps(steps)
+            q = s.get_q()
+            el = time.perf_counter() - t0
+            t = s.time()[0]
+        return q, el, t
+
+    def oracle_run(prob, steps):
+        t0 = time.perf_counter()
+        r = Oracle(prob).run_steps(prob.q0, steps)
+        return r, time.perf_counter() - t0
+
+    out = {"mode": "accuracy", "host_threads": orc.threads(), "rows": []}
+    add = out["rows"].append
+    # C1: 2D acoustics 128^2, 100 steps
+    prob = inputs.acoustics_2d_pulse(128)
+    ref, el_o = oracle_run(prob, 100)
+    q64, el64, _ = gpu(prob, 100, 64)
+    q32, el32, _ = gpu(prob, 100, 32)
+    add({"config": "C1 acoustics 128^2, 100 steps", "cells_x_steps": prob.ncells * 100,
+         "oracle_s": el_o, "fp64_s": el64, "fp32_s": el32,
+         "fp64_rel_linf": linf(q64, ref["q"]), "fp32_rel_l2": l2(q32, ref["q"])})
+    # C2: 4096^2 dam break, 200 steps
+    prob = inputs.sw_radial_dam_break(4096)
+    ref, el_o = oracle_run(prob, 200)
+    q64, el64, _ = gpu(prob, 200, 64)
+    q32, el32, _ = gpu(prob, 200, 32)
+    add({"config": "C2 shallow water 4096^2, 200 steps", "cells_x_steps": prob.ncells * 200,
+         "oracle_s": el_o, "fp64_s": el64, "fp32_s": el32,
+         "fp64_rel_linf": linf(q64, ref["q"]),
+         "fp32_rel_l1_h": orc.rel_l1(q32[0], ref["q"][0]),
+         "fp32_rel_l1_h_minus_1": orc.rel_l1(q32[0] - 1.0, ref["q"][0] - 1.0)})
+    # C3: 512^3 two-layer acoustics: 2 steps against the oracle, 100 steps
+    # FP32 against FP64
+    prob = inputs.acoustics_3d_layers(512)
+    ref, el_o = oracle_run(prob, 2)
+    q64, _, _ = gpu(prob, 2, 64)
+    q32, _, _ = gpu(prob, 2, 32)
+    q64b, el64, _ = gpu(prob, 100, 64)
+    q32b, el32, _ = gpu(prob, 100, 32)
+    add({"config": "C3 3D acoustics 512^3", "oracle_s_2_steps": el_o,
+         "fp64_s_100_steps": el64, "fp32_s_100_steps": el32,
+         "fp64_rel_linf_2_steps_vs_oracle": linf(q64, ref["q"]),
+         "fp32_rel_l2_2_steps_vs_oracle": l2(q32, ref["q"]),
+         "fp32_rel_l2_100_steps_vs_fp64_gpu": l2(q32b, q64b)})
+    # C4: 256-grid SW ensemble, 50 steps; 12 instances against the oracle
+    probs = inputs.sw_ensemble()
+    sizes = [p.n[0] for p in probs]
+    sample = sorted(set([0, 1, 2, 3, 64, 128, 200, 255, int(np.argmin(sizes)), int(np.argmax(sizes))]))
+    res = {}
+    for prec in (32, 64):
+        e = Ensemble.from_problems(probs, precision=prec)
+        e.autotune(1)
+        e.run_steps(50)
+        res[prec] = {i: e.get_q(i) for i in sample}
+        e.close()
+    e64, e32, e32p = 0.0, 0.0, 0.0
+    for i in sample:
+        ref = Oracle(probs[i]).run_steps(probs[i].q0, 50)["q"]
+        e64 = max(e64, linf(res[64][i], ref))
+        e32 = max(e32, orc.rel_l1(res[32][i][0], ref[0]))
+        e32p = max(e32p, orc.rel_l1(res[32][i][0] - 1.0, ref[0] - 1.0))
+    add({"config": "C4 SW ensemble, 256 grids, 50 steps", "instances_checked": len(sample),
+         "fp64_rel_linf_max": e64, "fp32_rel_l1_h_max": e32, "fp32_rel_l1_h_minus_1_max": e32p})
+    # C5: 64-cube acoustics ensemble, 100 steps, FP32 batched against FP64
+    # per instance (every instance)
+    probs = inputs.acoustics3d_ensemble()
+    e = Ensemble.from_problems(probs, precision=32)
+    e.autotune(1)
+    e.run_steps(100)
+    worst = 0.0
+    for i, p in enumerate(probs):
+        with Solver.from_problem(p, precision=64) as s:
+            s.run_steps(100)
+            worst = max(worst, l2(e.get_q(i), s.get_q()))
+    e.close()
+    add({"config": "C5 3D acoustics ensemble, 64 cubes, 100 steps", "instances_checked": len(probs),
+         "fp32_rel_l2_vs_fp64_gpu_max": worst})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def extra_ensembles(args):
     """Batched FP32 ensembles (one launch per sweep for all instances) against
     the plain FP64 path run instance by instance on the same instances."""
@@ -367,6 +469,8 @@ def main():
                     help="per-sweep times at the sizes of the paper's kernel tables (one JSON line)")
     ap.add_argument("--size-scaling", action="store_true",
                     help="cell-updates/s from 256^2 to 16384^2 (one JSON line)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="errors of every workload against the oracle, with times (one JSON line)")
     ap.add_argument("--fixed-segments", action="store_true",
                     help="with --paper-tables: 64-cell segments, no autotuning (for ncu)")
     args = ap.parse_args()
@@ -374,7 +478,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
-    if args.paper_tables or args.size_scaling:
+    if args.paper_tables or args.size_scaling or args.accuracy:
         import torch
         torch.cuda.set_device(0)
         if args.paper_tables:
@@ -383,6 +487,8 @@ def main():
             paper_tables(args)
         if args.size_scaling:
             size_scaling(args)
+        if args.accuracy:
+            accuracy(args)
         return 0
 
     rank, world, local = dist_env()
