@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-_SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2}
+_SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3}
 _LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 _BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 _SPLITTINGS = {"godunov": 0, "strang": 1}
@@ -33,7 +33,7 @@ class _Problem(C.Structure):
         ("rho", C.c_double), ("K", C.c_double), ("g", C.c_double),
         ("cfl_desired", C.c_double), ("cfl_max", C.c_double), ("dt_max", C.c_double),
         ("max_retries", C.c_int), ("rho_cell", _dp), ("K_cell", _dp),
-        ("splitting", C.c_int),
+        ("splitting", C.c_int), ("B_cell", _dp),
     ]
 
 
@@ -65,6 +65,9 @@ def lib():
                                        C.c_double, _dp, _dp, _dp, _dp]
         L.orc_rp_shallow_water.restype = None
         L.orc_rp_shallow_water.argtypes = [_dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_rp_shallow_water_bathy.restype = None
+        L.orc_rp_shallow_water_bathy.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
+                                                 _dp, _dp, _dp, _dp]
         L.orc_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -102,8 +105,12 @@ class Oracle:
             k = np.ascontiguousarray(prob.K_cell, dtype=np.float64)
             self._keep += [r, k]
             P.rho_cell, P.K_cell = _ptr(r), _ptr(k)
+        if prob.system == "shallow_water_bathy":
+            b = np.ascontiguousarray(prob.B_cell, dtype=np.float64)
+            self._keep.append(b)
+            P.B_cell = _ptr(b)
         self.P = P
-        self.m = 3 if prob.system == "shallow_water" else prob.ndim + 1
+        self.m = 3 if prob.system.startswith("shallow_water") else prob.ndim + 1
         self.shape = (self.m,) + tuple(reversed(prob.n))
 
     def _q(self, q):
@@ -152,8 +159,9 @@ class Oracle:
         return self._run(q, 1, 0, t_final, fixed_dt, t, dt)
 
 
-def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81):
-    """Waves W[p][c], speeds s[p], A-dQ, A+dQ at one interface (reduced states)."""
+def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81, B_l=0.0, B_r=0.0):
+    """Waves W[p][c] (f-waves for shallow_water_bathy), speeds s[p], A-dQ, A+dQ
+    at one interface (reduced states)."""
     ql = np.ascontiguousarray(np.pad(np.asarray(ql, dtype=np.float64), (0, 3 - len(ql))))
     qr = np.ascontiguousarray(np.pad(np.asarray(qr, dtype=np.float64), (0, 3 - len(qr))))
     W = np.zeros((3, 3))
@@ -163,6 +171,10 @@ def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81)
     if system == "shallow_water":
         lib().orc_rp_shallow_water(_ptr(ql), _ptr(qr), float(g), _ptr(W), _ptr(s),
                                    _ptr(am), _ptr(ap))
+        return W, s, am, ap
+    if system == "shallow_water_bathy":
+        lib().orc_rp_shallow_water_bathy(_ptr(ql), _ptr(qr), float(B_l), float(B_r), float(g),
+                                         _ptr(W), _ptr(s), _ptr(am), _ptr(ap))
         return W, s, am, ap
     lib().orc_rp_acoustics(_ptr(ql), _ptr(qr), float(rho_l), float(K_l), float(rho_r),
                            float(K_r), _ptr(W), _ptr(s), _ptr(am), _ptr(ap))

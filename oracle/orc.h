@@ -31,7 +31,10 @@
 extern "C" {
 #endif
 
-enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2 };
+/* ORC_SHALLOW_WATER_BATHY: shallow water over a bottom elevation B per
+ * cell, in the f-wave form (the returned "waves" are f-waves Z_p, and the
+ * correction term uses sign(s_p) instead of |s_p|). */
+enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2, ORC_SHALLOW_WATER_BATHY = 3 };
 /* ORC_LIM_NONE: unlimited second-order correction (Lax-Wendroff);
  * ORC_LIM_FIRST_ORDER: no correction at all (Godunov's first-order upwind
  * method: the Riemann solution and the fluctuation update alone). */
@@ -58,6 +61,7 @@ typedef struct {
     const double *rho_cell;/* per-cell rho, K (ORC_ACOUSTICS_VAR), else NULL */
     const double *K_cell;
     int splitting;         /* ORC_SPLIT_* */
+    const double *B_cell;  /* bottom elevation per cell (ORC_SHALLOW_WATER_BATHY), else NULL */
 } orc_problem;
 
 /* Number of state fields m and waves mwaves for a problem. */
@@ -71,6 +75,10 @@ void orc_rp_acoustics(const double *ql, const double *qr,
                       double W[3][3], double s[3], double amdq[3], double apdq[3]);
 void orc_rp_shallow_water(const double *ql, const double *qr, double g,
                           double W[3][3], double s[3], double amdq[3], double apdq[3]);
+/* f-waves W[p][c] = Z_p of the bathymetry system (see orc_shallow_water.c). */
+void orc_rp_shallow_water_bathy(const double *ql, const double *qr, double B_l, double B_r,
+                                double g, double W[3][3], double s[3], double amdq[3],
+                                double apdq[3]);
 
 /* Wave limiter function phi(theta), minmod or MC; ORC_LIM_NONE gives 1. */
 double orc_phi(int limiter, double theta);

@@ -113,3 +113,69 @@ void orc_rp_shallow_water(const double *ql, const double *qr, double g,
         }
     }
 }
+
+/*
+ * Shallow water over bathymetry B(x) (bottom elevation), the source term
+ * (0, -g h B_x, -g h B_y) of Sec. 3's Clawpack base (source terms are added
+ * to the hyperbolic part there) folded into the Riemann problem as f-waves,
+ * the well-balanced form of the wave-propagation method:
+ *
+ *   psi  = (0, -g h_bar (B_r - B_l), 0)              source across the interface
+ *   delta = f(Q_r) - f(Q_l) - psi = sum_p Z_p,        Z_p = beta_p r_p
+ * with the Roe speeds and eigenvectors above.  The momentum component uses
+ * g (h_r^2 - h_l^2) / 2 = g h_bar (h_r - h_l):
+ *   delta_0 = (hu)_r - (hu)_l
+ *   delta_1 = (hu u)_r - (hu u)_l + g h_bar ((h_r - h_l) + (B_r - B_l))
+ *   delta_2 = (hu v)_r - (hu v)_l
+ * so a lake at rest (u = v = 0, h + B constant) gives delta = 0 exactly.
+ *   beta_1 = ((u_hat + c_hat) delta_0 - delta_1) / (2 c_hat)
+ *   beta_2 = delta_2 - v_hat delta_0
+ *   beta_3 = (delta_1 - (u_hat - c_hat) delta_0) / (2 c_hat)
+ * Fluctuations: A-dQ = sum of Z_p with s_p < 0, A+dQ = sum of the others.
+ * No entropy fix.  Returns the f-waves in W.
+ */
+void orc_rp_shallow_water_bathy(const double *ql, const double *qr, double B_l, double B_r,
+                                double g, double W[3][3], double s[3], double amdq[3],
+                                double apdq[3])
+{
+    double h_l = ql[0], h_r = qr[0];
+    double u_l = ql[1] / h_l, u_r = qr[1] / h_r;
+    double v_l = ql[2] / h_l, v_r = qr[2] / h_r;
+    double sqh_l = sqrt(h_l), sqh_r = sqrt(h_r);
+
+    double h_bar = 0.5 * (h_l + h_r);
+    double u_hat = (sqh_l * u_l + sqh_r * u_r) / (sqh_l + sqh_r);
+    double v_hat = (sqh_l * v_l + sqh_r * v_r) / (sqh_l + sqh_r);
+    double c_hat = sqrt(g * h_bar);
+
+    double delta0 = qr[1] - ql[1];
+    double delta1 = (qr[1] * u_r - ql[1] * u_l) + g * h_bar * ((h_r - h_l) + (B_r - B_l));
+    double delta2 = qr[1] * v_r - ql[1] * v_l;
+
+    double beta1 = ((u_hat + c_hat) * delta0 - delta1) / (2.0 * c_hat);
+    double beta2 = delta2 - v_hat * delta0;
+    double beta3 = (delta1 - (u_hat - c_hat) * delta0) / (2.0 * c_hat);
+
+    s[0] = u_hat - c_hat;
+    s[1] = u_hat;
+    s[2] = u_hat + c_hat;
+
+    W[0][0] = beta1;
+    W[0][1] = beta1 * (u_hat - c_hat);
+    W[0][2] = beta1 * v_hat;
+    W[1][0] = 0.0;
+    W[1][1] = 0.0;
+    W[1][2] = beta2;
+    W[2][0] = beta3;
+    W[2][1] = beta3 * (u_hat + c_hat);
+    W[2][2] = beta3 * v_hat;
+
+    for (int c = 0; c < 3; ++c) {
+        amdq[c] = 0.0;
+        apdq[c] = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            if (s[p] < 0.0) amdq[c] += W[p][c];
+            else            apdq[c] += W[p][c];
+        }
+    }
+}

@@ -30,15 +30,20 @@
 #endif
 #include "orc.h"
 
+static int is_sw(const orc_problem *P)
+{
+    return P->system == ORC_SHALLOW_WATER || P->system == ORC_SHALLOW_WATER_BATHY;
+}
+
 int orc_m(const orc_problem *P)
 {
-    if (P->system == ORC_SHALLOW_WATER) return 3;
+    if (is_sw(P)) return 3;
     return P->ndim + 1;
 }
 
 int orc_mwaves(const orc_problem *P)
 {
-    return P->system == ORC_SHALLOW_WATER ? 3 : 2;
+    return is_sw(P) ? 3 : 2;
 }
 
 int orc_threads(void)
@@ -53,7 +58,7 @@ int orc_threads(void)
 /* Components of the reduced state along d, as field indices. */
 static int nq_of(const orc_problem *P)
 {
-    return P->system == ORC_SHALLOW_WATER ? 3 : 2;
+    return is_sw(P) ? 3 : 2;
 }
 
 static int field_of(const orc_problem *P, int d, int c)
@@ -121,11 +126,13 @@ double orc_phi(int limiter, double theta)
 }
 
 static void riemann(const orc_problem *P, const double *ql, const double *qr,
-                    double rho_l, double K_l, double rho_r, double K_r,
+                    double rho_l, double K_l, double rho_r, double K_r, double B_l, double B_r,
                     double W[3][3], double s[3], double amdq[3], double apdq[3])
 {
     if (P->system == ORC_SHALLOW_WATER)
         orc_rp_shallow_water(ql, qr, P->g, W, s, amdq, apdq);
+    else if (P->system == ORC_SHALLOW_WATER_BATHY)
+        orc_rp_shallow_water_bathy(ql, qr, B_l, B_r, P->g, W, s, amdq, apdq);
     else
         orc_rp_acoustics(ql, qr, rho_l, K_l, rho_r, K_r, W, s, amdq, apdq);
 }
@@ -134,6 +141,7 @@ static void riemann(const orc_problem *P, const double *ql, const double *qr,
 typedef struct {
     double (*q)[3];        /* cells -2..N+1 at index i+2 */
     double *rho, *K;       /* same indexing */
+    double *B;             /* bottom elevation, same indexing */
     double (*W)[3][3];     /* interfaces -1..N+1 at index I+1 */
     double (*s)[3];
     double (*amdq)[3];
@@ -148,6 +156,7 @@ static void work_alloc(line_work *w, int N)
     w->q = malloc(sizeof(double[3]) * (N + 4));
     w->rho = malloc(sizeof(double) * (N + 4));
     w->K = malloc(sizeof(double) * (N + 4));
+    w->B = malloc(sizeof(double) * (N + 4));
     w->W = malloc(sizeof(double[3][3]) * (N + 3));
     w->s = malloc(sizeof(double[3]) * (N + 3));
     w->amdq = malloc(sizeof(double[3]) * (N + 3));
@@ -159,7 +168,7 @@ static void work_alloc(line_work *w, int N)
 
 static void work_free(line_work *w)
 {
-    free(w->q); free(w->rho); free(w->K); free(w->W); free(w->s);
+    free(w->q); free(w->rho); free(w->K); free(w->B); free(w->W); free(w->s);
     free(w->amdq); free(w->apdq); free(w->Wt); free(w->F); free(w->qnew);
 }
 
@@ -178,6 +187,7 @@ static void gather_line(const orc_problem *P, int d, long line, const double *qi
             double v = qin[(long)field_of(P, d, c) * ncell + idx];
             w->q[i + 2][c] = (c == 1) ? sign * v : v;
         }
+        w->B[i + 2] = P->system == ORC_SHALLOW_WATER_BATHY ? P->B_cell[idx] : 0.0;
         if (P->system == ORC_ACOUSTICS_VAR) {
             w->rho[i + 2] = P->rho_cell[idx];
             w->K[i + 2] = P->K_cell[idx];
@@ -198,7 +208,7 @@ static double update_line(const orc_problem *P, int d, double nu, line_work *w)
     /* 1. Riemann problems at interfaces I = -1..N+1 (between cells I-1, I). */
     for (int I = -1; I <= N + 1; ++I) {
         int L = I - 1 + 2, R = I + 2;   /* array positions of cells I-1, I */
-        riemann(P, w->q[L], w->q[R], w->rho[L], w->K[L], w->rho[R], w->K[R],
+        riemann(P, w->q[L], w->q[R], w->rho[L], w->K[L], w->rho[R], w->K[R], w->B[L], w->B[R],
                 w->W[I + 1], w->s[I + 1], w->amdq[I + 1], w->apdq[I + 1]);
     }
 
@@ -226,13 +236,17 @@ static double update_line(const orc_problem *P, int d, double nu, line_work *w)
         }
     }
 
-    /* 3. Correction flux F_I = 1/2 sum_p |s_p| (1 - nu |s_p|) W~_p. */
+    /* 3. Correction flux F_I = 1/2 sum_p |s_p| (1 - nu |s_p|) W~_p; for
+     *    f-waves Z_p = s_p W_p the factor |s_p| becomes sign(s_p). */
+    int fwave = P->system == ORC_SHALLOW_WATER_BATHY;
     for (int I = 0; I <= N; ++I) {
         for (int c = 0; c < nq; ++c) {
             double acc = 0.0;
             for (int p = 0; p < nw; ++p) {
-                double as = fabs(w->s[I + 1][p]);
-                acc += as * (1.0 - nu * as) * w->Wt[I + 1][p][c];
+                double sp = w->s[I + 1][p];
+                double as = fabs(sp);
+                double k = fwave ? (sp > 0.0 ? 1.0 : (sp < 0.0 ? -1.0 : 0.0)) : as;
+                acc += k * (1.0 - nu * as) * w->Wt[I + 1][p][c];
             }
             w->F[I + 1][c] = 0.5 * acc;
         }
@@ -319,7 +333,7 @@ double orc_max_speed_dir(const orc_problem *P, int d, const double *q)
             for (int I = 0; I <= N; ++I) {
                 double W[3][3], s[3], amdq[3], apdq[3];
                 int L = I + 1, R = I + 2;
-                riemann(P, w.q[L], w.q[R], w.rho[L], w.K[L], w.rho[R], w.K[R],
+                riemann(P, w.q[L], w.q[R], w.rho[L], w.K[L], w.rho[R], w.K[R], w.B[L], w.B[R],
                         W, s, amdq, apdq);
                 for (int p = 0; p < nw; ++p)
                     if (fabs(s[p]) > mmax) mmax = fabs(s[p]);

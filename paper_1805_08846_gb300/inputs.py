@@ -23,7 +23,7 @@ import numpy as np
 
 SEED = 1805
 
-SYSTEMS = ("acoustics", "acoustics_var", "shallow_water")
+SYSTEMS = ("acoustics", "acoustics_var", "shallow_water", "shallow_water_bathy")
 LIMITERS = ("none", "minmod", "mc", "first_order")
 BCS = ("periodic", "extrap", "wall")
 SPLITTINGS = ("godunov", "strang")
@@ -51,6 +51,7 @@ class Problem:
     K_cell: Optional[np.ndarray] = None
     name: str = ""
     splitting: str = "godunov"    # one of SPLITTINGS
+    B_cell: Optional[np.ndarray] = None     # (ny, nx) bottom elevation for shallow_water_bathy
 
     @property
     def m(self) -> int:
@@ -58,7 +59,7 @@ class Problem:
 
     @property
     def mwaves(self) -> int:
-        return 3 if self.system == "shallow_water" else 2
+        return 3 if self.system.startswith("shallow_water") else 2
 
     @property
     def dx(self) -> tuple:
@@ -113,6 +114,24 @@ def sw_radial_dam_break(n: int = 4096, ny: Optional[int] = None, limiter: str = 
     q0[0] = np.where(r < radius, h_in, h_out)
     return Problem(2, (n, ny), (-1.0, -1.0), (1.0, 1.0), "shallow_water", limiter,
                    (bc,) * 4, q0, g=9.81, nsteps=nsteps, name=f"sw_radial_dam_break_{n}x{ny}")
+
+
+def sw_bathymetry(n: int = 4096, limiter: str = "minmod", bc: str = "extrap", nsteps: int = 200,
+                  bump: float = 0.5, hump: float = 0.2) -> Problem:
+    """Shallow water over bathymetry on [-1,1]^2: a Gaussian seamount
+    B = bump exp(-20 ((x-0.3)^2 + y^2)) under a surface at rest at 1, with a
+    Gaussian surface hump eta = 1 + hump exp(-40 ((x+0.4)^2 + y^2)) that runs
+    over it; zero momentum.  B and eta are rounded to multiples of 2^-24, so
+    h = eta - B is exact and the resting part of the surface is exactly flat."""
+    x = centres(n, -1.0, 1.0)
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    q = 2.0 ** -24
+    B = np.round(bump * np.exp(-20.0 * ((X - 0.3) ** 2 + Y ** 2)) / q) * q
+    eta = 1.0 + np.round(hump * np.exp(-40.0 * ((X + 0.4) ** 2 + Y ** 2)) / q) * q
+    q0 = np.zeros((3, n, n))
+    q0[0] = eta - B
+    return Problem(2, (n, n), (-1.0, -1.0), (1.0, 1.0), "shallow_water_bathy", limiter,
+                   (bc,) * 4, q0, nsteps=nsteps, B_cell=B, name=f"sw_bathymetry_{n}")
 
 
 def acoustics_3d_layers(n: int = 512, width: float = 200.0, limiter: str = "mc",
@@ -230,7 +249,8 @@ def random_smooth_state(problem_system: str, shape: Sequence[int], seed: int = S
     box. Shallow water gets h = 1 + perturbation (> 0.4 everywhere)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     ndim = len(shape)
-    m = 3 if problem_system == "shallow_water" else (ndim + 1)
+    sw = problem_system.startswith("shallow_water")
+    m = 3 if sw else (ndim + 1)
     coords = np.meshgrid(*[centres(s, 0.0, 1.0) for s in shape], indexing="ij")
     q = np.zeros((m,) + tuple(shape))
     for f in range(m):
@@ -242,7 +262,7 @@ def random_smooth_state(problem_system: str, shape: Sequence[int], seed: int = S
             for d in range(ndim):
                 mode = mode * np.cos(2 * np.pi * k[d] * coords[d] + ph[d])
             q[f] += a * mode
-    if problem_system == "shallow_water":
+    if sw:
         q[0] += 1.0
     return q
 
@@ -261,11 +281,14 @@ def random_problem(system: str, shape_xyz: Sequence[int], limiter: str, bc,
         q0[(0,) + tuple(sl)] += 0.5
     if isinstance(bc, str):
         bc = (bc,) * (2 * ndim)
-    rho_cell = K_cell = None
+    rho_cell = K_cell = B_cell = None
     if system == "acoustics_var":
         rng = np.random.Generator(np.random.PCG64(seed + 7))
         rho_cell = box_filter5(np.exp(rng.uniform(np.log(0.5), np.log(4.0), size=arr_shape)))
         K_cell = box_filter5(np.exp(rng.uniform(np.log(0.5), np.log(4.0), size=arr_shape)))
+    if system == "shallow_water_bathy":
+        # smooth random bottom within [-0.2, 0.2] (the depth stays > 0.2)
+        B_cell = 0.6 * random_smooth_state("acoustics", arr_shape, seed=seed + 11, amplitude=0.1)[0]
     return Problem(ndim, tuple(shape_xyz), (0.0,) * ndim, (1.0,) * ndim, system, limiter,
-                   tuple(bc), q0, rho=1.0, K=4.0, rho_cell=rho_cell, K_cell=K_cell,
+                   tuple(bc), q0, rho=1.0, K=4.0, rho_cell=rho_cell, K_cell=K_cell, B_cell=B_cell,
                    name=f"{system}_{'x'.join(map(str, shape_xyz))}_{limiter}")

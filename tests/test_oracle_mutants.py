@@ -17,7 +17,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 
-# (file, original text, mutated text, what the slip is)
+# (file, original text, mutated text, what the slip is[, n]): the text must
+# be unique in the file, or n picks its n-th occurrence (lines the Roe and
+# the bathymetry solvers share)
 MUTANTS = [
     ("orc_acoustics.c", "double alpha2 = (dp + Z_l * du) / (Z_l + Z_r);",
      "double alpha2 = (dp - Z_l * du) / (Z_l + Z_r);", "sign of a wave strength"),
@@ -28,19 +30,19 @@ MUTANTS = [
      "double alpha2 = d2 - u_hat * d0;", "shear strength uses the normal velocity"),
     ("orc_shallow_water.c",
      "double u_hat = (sqh_l * u_l + sqh_r * u_r) / (sqh_l + sqh_r);",
-     "double u_hat = (sqh_r * u_l + sqh_l * u_r) / (sqh_l + sqh_r);", "Roe weights swapped"),
+     "double u_hat = (sqh_r * u_l + sqh_l * u_r) / (sqh_l + sqh_r);", "Roe weights swapped", 1),
     ("orc_shallow_water.c", "double beta = (lam_m - s[0]) / (lam_m - lam_l);",
      "double beta = (s[0] - lam_l) / (lam_m - lam_l);", "entropy-fix fraction transposed"),
     ("orc_shallow_water.c", "if (lam_l < 0.0 && 0.0 < lam_m) {",
      "if (lam_l < 0.0 || 0.0 < lam_m) {", "entropy fix triggers off the sonic point"),
     ("orc_shallow_water.c", "double c_hat = sqrt(g * h_bar);",
-     "double c_hat = sqrt(g * h_r);", "Roe celerity from one side"),
+     "double c_hat = sqrt(g * h_r);", "Roe celerity from one side", 1),
     ("orc_wavesweep.c", "int J = w->s[I + 1][p] > 0.0 ? I - 1 : I + 1;",
      "int J = w->s[I + 1][p] > 0.0 ? I + 1 : I - 1;", "limiter looks downwind"),
     ("orc_wavesweep.c", "if (dot_ii != 0.0) phi = orc_phi(P->limiter, dot_ji / dot_ii);",
      "if (dot_ji != 0.0) phi = orc_phi(P->limiter, dot_ii / dot_ji);", "theta ratio inverted"),
-    ("orc_wavesweep.c", "acc += as * (1.0 - nu * as) * w->Wt[I + 1][p][c];",
-     "acc += as * w->Wt[I + 1][p][c];", "dropped (1 - nu|s|) factor"),
+    ("orc_wavesweep.c", "acc += k * (1.0 - nu * as) * w->Wt[I + 1][p][c];",
+     "acc += k * w->Wt[I + 1][p][c];", "dropped (1 - nu|s|) factor"),
     ("orc_wavesweep.c", "w->F[I + 1][c] = 0.5 * acc;", "w->F[I + 1][c] = acc;",
      "dropped 1/2 in the correction flux"),
     ("orc_wavesweep.c", "double first = w->apdq[i + 1][c] + w->amdq[i + 2][c];",
@@ -65,10 +67,18 @@ MUTANTS = [
      "first-order method keeps the unlimited correction"),
     ("orc_wavesweep.c", "dirs[n] = P->ndim - 1; frac[n] = 1.0; ++n;",
      "dirs[n] = P->ndim - 1; frac[n] = 0.5; ++n;", "Strang middle sweep takes half a step"),
+    ("orc_shallow_water.c", "g * h_bar * ((h_r - h_l) + (B_r - B_l));",
+     "g * h_bar * (h_r - h_l);", "bathymetry source dropped"),
+    ("orc_shallow_water.c", "g * h_bar * ((h_r - h_l) + (B_r - B_l));",
+     "g * h_bar * ((h_r - h_l) - (B_r - B_l));", "bathymetry source with the wrong sign"),
+    ("orc_shallow_water.c", "g * h_bar * ((h_r - h_l) + (B_r - B_l));",
+     "g * h_r * ((h_r - h_l) + (B_r - B_l));", "source depth from one side"),
+    ("orc_wavesweep.c", "double k = fwave ? (sp > 0.0 ? 1.0 : (sp < 0.0 ? -1.0 : 0.0)) : as;",
+     "double k = as;", "f-wave correction weighted by |s| instead of sign(s)"),
 ]
 
 
-def _build_mutant(tmp, fname, old, new):
+def _build_mutant(tmp, fname, old, new, nth=None):
     src_dir = os.path.join(tmp, "src")
     os.makedirs(src_dir, exist_ok=True)
     for f in os.listdir(ORACLE):
@@ -76,8 +86,16 @@ def _build_mutant(tmp, fname, old, new):
             shutil.copy(os.path.join(ORACLE, f), src_dir)
     path = os.path.join(src_dir, fname)
     text = open(path).read()
-    assert text.count(old) == 1, f"pattern not unique in {fname}: {old!r}"
-    open(path, "w").write(text.replace(old, new))
+    if nth is None:
+        assert text.count(old) == 1, f"pattern not unique in {fname}: {old!r}"
+        text = text.replace(old, new)
+    else:
+        assert text.count(old) >= nth, f"pattern occurs fewer than {nth} times in {fname}"
+        at = -1
+        for _ in range(nth):
+            at = text.index(old, at + 1)
+        text = text[:at] + new + text[at + len(old):]
+    open(path, "w").write(text)
     lib = os.path.join(tmp, "libmut.so")
     cfiles = [os.path.join(src_dir, f) for f in sorted(os.listdir(src_dir)) if f.endswith(".c")]
     subprocess.run(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-fopenmp",
@@ -85,9 +103,10 @@ def _build_mutant(tmp, fname, old, new):
     return lib
 
 
-@pytest.mark.parametrize("fname,old,new,what", MUTANTS, ids=[m[3] for m in MUTANTS])
-def test_pins_catch_planted_mistake(tmp_path, fname, old, new, what):
-    lib = _build_mutant(str(tmp_path), fname, old, new)
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[3] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, mutant):
+    fname, old, new, what = mutant[:4]
+    lib = _build_mutant(str(tmp_path), fname, old, new, *mutant[4:])
     env = dict(os.environ, ORC_LIB=lib, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],

@@ -631,3 +631,90 @@ def test_advance_lands_on_t_final():
     r = Oracle(p).advance(p.q0, 0.01)
     assert r["t"] == 0.01
     assert r["nacc"] >= 1
+
+
+# ---------------------------------------------------------------- bathymetry
+
+def sw_flux_with_source_jump(ql, qr, B_l, B_r, g=G):
+    """f(Q_r) - f(Q_l) - psi with psi = (0, -g h_bar (B_r - B_l), 0)."""
+    fl, fr = sw_flux(np.asarray(ql, float)), sw_flux(np.asarray(qr, float))
+    hbar = 0.5 * (ql[0] + qr[0])
+    return fr - fl - np.array([0.0, -g * hbar * (B_r - B_l), 0.0])
+
+
+def test_bathymetry_fwaves_decompose_flux_jump_minus_source():
+    """The f-waves sum to f(Q_r) - f(Q_l) - psi, each lies on its Roe
+    eigenvector (Z_p = beta_p (1, s_p, v_hat) for p = 1, 3; Z_2 = (0, 0, .)),
+    and the fluctuations split the same sum by the sign of s_p."""
+    rng = np.random.default_rng(51)
+    for _ in range(200):
+        ql = np.array([rng.uniform(0.2, 3.0), rng.uniform(-2, 2), rng.uniform(-2, 2)])
+        qr = np.array([rng.uniform(0.2, 3.0), rng.uniform(-2, 2), rng.uniform(-2, 2)])
+        B_l, B_r = rng.uniform(-0.5, 0.5, size=2)
+        Z, s, am, ap = oracle.riemann("shallow_water_bathy", ql, qr, B_l=B_l, B_r=B_r)
+        delta = sw_flux_with_source_jump(ql, qr, B_l, B_r)
+        scale = np.abs(delta).max() + 1.0
+        assert np.abs(Z.sum(axis=0) - delta).max() <= 1e-13 * scale
+        assert np.abs(am + ap - delta).max() <= 1e-13 * scale
+        for p in (0, 2):
+            assert abs(Z[p][1] - s[p] * Z[p][0]) <= 1e-13 * scale
+        assert Z[1][0] == 0.0 and Z[1][1] == 0.0
+        np.testing.assert_allclose(am, sum(Z[p] for p in range(3) if s[p] < 0) + 0 * am, atol=1e-14 * scale)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "extrap", "wall"])
+@pytest.mark.parametrize("limiter", ["none", "minmod", "mc", "first_order"])
+def test_bathymetry_lake_at_rest_bitwise(bc, limiter):
+    """Well-balanced: a flat surface at rest over a seamount stays exactly at
+    rest (the flux jump and the source cancel at every interface)."""
+    p = inputs.sw_bathymetry(48, limiter=limiter, bc=bc, hump=0.0)
+    r = Oracle(p).run_steps(p.q0, 8)["q"]
+    np.testing.assert_array_equal(r, p.q0)
+
+
+def test_bathymetry_momentum_changes_by_the_source_only():
+    """Periodic, y-uniform data: one step keeps sum h and sum hv, and sum hu
+    changes by exactly -nu g sum_I h_bar_I (B_I - B_{I-1}) over the N
+    interfaces (the fluctuations telescope except for the source; the
+    correction fluxes telescope)."""
+    N, ny = 64, 2
+    rng = np.random.default_rng(57)
+    x = inputs.centres(N, 0.0, 1.0)
+    B = 0.2 * np.sin(2 * np.pi * x) + 0.05 * np.cos(6 * np.pi * x)
+    h = 1.0 + 0.1 * np.cos(2 * np.pi * x + 0.3)
+    hu = 0.2 * np.sin(4 * np.pi * x)
+    hv = 0.1 * np.cos(2 * np.pi * x)
+    q0 = np.repeat(np.stack([h, hu, hv])[:, None, :], ny, axis=1)
+    p = line_problem("shallow_water_bathy", N, ny=ny, limiter="mc", q0=q0,
+                     B_cell=np.repeat(B[None, :], ny, axis=0))
+    dt = 0.3 * p.dx[0] / 4.0
+    r = Oracle(p).run_steps(q0, 1, fixed_dt=dt)["q"]
+    nu = dt / p.dx[0]
+    hbar = 0.5 * (h + np.roll(h, 1))
+    dB = B - np.roll(B, 1)
+    expect = hu.sum() - nu * G * np.sum(hbar * dB)
+    assert abs(r[0][0].sum() - h.sum()) <= 1e-13 * h.sum()
+    assert abs(r[1][0].sum() - expect) <= 1e-13 * np.abs(hu).sum()
+    assert abs(r[2][0].sum() - hv.sum()) <= 1e-13 * np.abs(hv).sum()
+
+
+@pytest.mark.parametrize("limiter", ["none", "first_order"])
+def test_bathymetry_flat_bottom_matches_shallow_water(limiter):
+    """With a flat bottom psi = 0 and, by the Roe property, Z_p = s_p W_p; the
+    f-wave correction 1/2 sign(s)(1 - nu|s|) Z then equals 1/2 |s|(1 - nu|s|) W,
+    so without a limiter (and in first order) the scheme is the shallow-water
+    scheme (subsonic data: no entropy fix)."""
+    pb = inputs.random_problem("shallow_water_bathy", (41, 33), limiter, "periodic")
+    pb = pb.with_(B_cell=np.full_like(pb.B_cell, 0.25))
+    ps = pb.with_(system="shallow_water", B_cell=None)
+    rb = Oracle(pb).run_steps(pb.q0, 6)
+    rs = Oracle(ps).run_steps(ps.q0, 6)
+    for f in range(3):
+        assert oracle.rel_linf(rb["q"][f], rs["q"][f]) <= 1e-12
+    assert rb["t"] == pytest.approx(rs["t"], rel=1e-14)
+
+
+def test_bathymetry_mass_conservation_periodic():
+    p = inputs.random_problem("shallow_water_bathy", (45, 38), "minmod", "periodic", discontinuous=True)
+    r = Oracle(p).run_steps(p.q0, 10)["q"]
+    assert abs(r[0].sum() - p.q0[0].sum()) <= 1e-13 * p.q0[0].sum()
