@@ -190,6 +190,32 @@ def extra_acoustics3d(args, peak_gbs):
     return out
 
 
+def extra_bathymetry(args, peak_gbs):
+    """Shallow water over a seamount (source term as f-waves, well-balanced),
+    4096^2, minmod, outflow: FP32 and FP64 cell-updates/s and the HBM
+    fraction of the dominant FP32 sweep (7 values of 4 B per cell and sweep:
+    h, hu, hv read and written, B read)."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    prob = inputs.sw_bathymetry(args.n)
+    out = {"workload": f"2D shallow water over a seamount {args.n}^2 (f-wave source), minmod, "
+                       f"outflow, CFL 0.9"}
+    for prec, steps in ((32, 100), (64, 5)):
+        s = Solver.from_problem(prob, precision=prec)
+        seg = s.autotune(2)
+        s.run_steps(3)
+        ms, tot, nl = s.profile_steps(steps)
+        s.close()
+        r = {"value": prob.ncells * steps / (tot * 1e-3), "ms_per_step": tot / steps,
+             "sweep_ms": ms[:2], "steps": steps, "segments": seg[:2]}
+        if prec == 32:
+            dom = int(np.argmax(ms[:2]))
+            ach = 28 * prob.ncells / (ms[dom] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+                             "frac": ach / peak_gbs, "kernel": f"sweep dir={'xy'[dom]}"}
+        out[f"f{prec}"] = r
+    return out
+
+
 # Sec. 7.1 (Tables 1-6): the paper's kernel-analysis problems.  Values a
 # sweep reads and writes per cell (fields it leaves unchanged are neither):
 # 2D acoustics p, u_d (2 + 2); shallow water h, hu, hv (3 + 3); 3D
@@ -581,6 +607,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         for key, fn in (("acoustics3d", lambda: extra_acoustics3d(args, peak_gbs)),
+                        ("sw_bathymetry", lambda: extra_bathymetry(args, peak_gbs)),
                         ("ensembles", lambda: extra_ensembles(args))):
             try:
                 extras[key] = fn()

@@ -20,6 +20,13 @@
  *   CLAW_ACOUSTICS_VAR  the same with per-cell rho, K (claw_set_aux).
  *   CLAW_SHALLOW_WATER  2D shallow water, m = 3 (h, hu, hv), mwaves = 3,
  *                       Roe solver with the Harten-Hyman entropy fix.
+ *   CLAW_SHALLOW_WATER_BATHY  2D shallow water over a bottom elevation B
+ *                       (claw_set_bathymetry; flat B = 0 until set): the
+ *                       source -g h grad B enters the Riemann problem as
+ *                       f-waves of f(Q_r) - f(Q_l) - (0, -g h_bar dB, 0) on
+ *                       the Roe eigenvectors (Sec. 3's Clawpack base adds
+ *                       source terms to the hyperbolic part), so a lake at
+ *                       rest stays exactly at rest; no entropy fix, h > 0.
  *
  * Conventions for every call:
  *   - State arrays crossing the boundary are FP64, structure of arrays,
@@ -62,7 +69,12 @@ typedef enum {
 } claw_status;
 
 typedef enum { CLAW_BC_PERIODIC = 0, CLAW_BC_EXTRAP = 1, CLAW_BC_WALL = 2 } claw_bc;
-typedef enum { CLAW_ACOUSTICS = 0, CLAW_ACOUSTICS_VAR = 1, CLAW_SHALLOW_WATER = 2 } claw_system;
+typedef enum {
+    CLAW_ACOUSTICS = 0,
+    CLAW_ACOUSTICS_VAR = 1,
+    CLAW_SHALLOW_WATER = 2,
+    CLAW_SHALLOW_WATER_BATHY = 3
+} claw_system;
 /* Second-order correction of Sec. 3 Eq. LW-update: NONE applies it
  * unlimited (Lax-Wendroff), MINMOD / MC limit each wave against its upwind
  * neighbour; FIRST_ORDER drops it (Godunov's first-order upwind method: the
@@ -132,6 +144,12 @@ claw_status claw_get_q(claw_solver* s, double* q_soa, int on_device);
  * not checked (the caller guarantees positivity). */
 claw_status claw_set_aux(claw_solver* s, const double* rho, const double* K, int on_device);
 
+/* Bottom elevation B per cell (nx*ny doubles, x fastest) for
+ * CLAW_SHALLOW_WATER_BATHY, stored in the state's precision (the wave
+ * speeds do not depend on it, so dt is unchanged).  CLAW_EINVAL for other
+ * systems.  Synchronises. */
+claw_status claw_set_bathymetry(claw_solver* s, const double* B, int on_device);
+
 /* One accepted step.  dt > 0: exactly that step, always kept (no CFL
  * control); dt <= 0: the CFL rule, redone on a violation.  *cfl_out (may be
  * NULL) receives the Courant number of the kept step.  Synchronises. */
@@ -182,6 +200,7 @@ claw_status claw_ensemble_set_q(claw_solver* s, int i, const double* q, int on_d
 claw_status claw_ensemble_get_q(claw_solver* s, int i, double* q, int on_device);
 claw_status claw_ensemble_set_aux(claw_solver* s, int i, const double* rho, const double* K,
                                   int on_device);
+claw_status claw_ensemble_set_bathymetry(claw_solver* s, int i, const double* B, int on_device);
 /* nsteps accepted steps for every instance, each under its own CFL rule. */
 claw_status claw_ensemble_run_steps(claw_solver* s, int nsteps);
 claw_status claw_ensemble_get_time(claw_solver* s, int i, double* t, double* dt, long* nsteps);

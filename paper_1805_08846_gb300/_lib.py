@@ -19,7 +19,7 @@ from . import build as _build
 CLAW_OK, CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA, CLAW_ECFL, CLAW_ENONPHYS, CLAW_ETIMEOUT, CLAW_EBOUNDS = range(8)
 STATUS_NAMES = {0: "CLAW_OK", 1: "CLAW_EINVAL", 2: "CLAW_ENOMEM", 3: "CLAW_ECUDA", 4: "CLAW_ECFL",
                 5: "CLAW_ENONPHYS", 6: "CLAW_ETIMEOUT", 7: "CLAW_EBOUNDS"}
-SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2}
+SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3}
 LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 
@@ -49,6 +49,7 @@ _SIGS = {
     "claw_set_q": [_vp, _vp, C.c_int],
     "claw_get_q": [_vp, _vp, C.c_int],
     "claw_set_aux": [_vp, _vp, _vp, C.c_int],
+    "claw_set_bathymetry": [_vp, _vp, C.c_int],
     "claw_step": [_vp, C.c_double, _dp],
     "claw_advance": [_vp, C.c_double, C.c_double, C.POINTER(C.c_int)],
     "claw_run_steps": [_vp, C.c_int],
@@ -63,6 +64,7 @@ _SIGS = {
     "claw_ensemble_set_q": [_vp, C.c_int, _vp, C.c_int],
     "claw_ensemble_get_q": [_vp, C.c_int, _vp, C.c_int],
     "claw_ensemble_set_aux": [_vp, C.c_int, _vp, _vp, C.c_int],
+    "claw_ensemble_set_bathymetry": [_vp, C.c_int, _vp, C.c_int],
     "claw_ensemble_run_steps": [_vp, C.c_int],
     "claw_ensemble_get_time": [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_long)],
     "claw_ensemble_size": [_vp],
@@ -208,6 +210,11 @@ def claw_set_aux(h, rho, K):
     _check(lib().claw_set_aux(h, pr, pk, dr), "claw_set_aux")
 
 
+def claw_set_bathymetry(h, B):
+    pb, db, kb = _array_arg(B)
+    _check(lib().claw_set_bathymetry(h, pb, db), "claw_set_bathymetry")
+
+
 def claw_step(h, dt=0.0):
     cfl = C.c_double(0.0)
     _check(lib().claw_step(h, float(dt), C.byref(cfl)), "claw_step")
@@ -267,6 +274,11 @@ def claw_ensemble_set_aux(h, i, rho, K):
     pr, dr, kr = _array_arg(rho)
     pk, dk, kk = _array_arg(K)
     _check(lib().claw_ensemble_set_aux(h, int(i), pr, pk, dr), "claw_ensemble_set_aux")
+
+
+def claw_ensemble_set_bathymetry(h, i, B):
+    pb, db, kb = _array_arg(B)
+    _check(lib().claw_ensemble_set_bathymetry(h, int(i), pb, db), "claw_ensemble_set_bathymetry")
 
 
 def claw_ensemble_run_steps(h, nsteps):

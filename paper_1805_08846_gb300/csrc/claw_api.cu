@@ -49,8 +49,15 @@ int slot_of_version(int v) { return v == 0 ? 0 : 1 + (v - 1) % 2; }
 
 // Fields a sweep along d changes (the reduced state of the Riemann solver).
 std::vector<int> touched_fields(int system, int d) {
-    if (system == kSysShallowWater) return {0, 1, 2};
+    if (system == kSysShallowWater || system == kSysShallowWaterBathy) return {0, 1, 2};
     return {0, 1 + d};
+}
+
+bool is_sw(int system) { return system == CLAW_SHALLOW_WATER || system == CLAW_SHALLOW_WATER_BATHY; }
+
+// Material planes per cell: (Z, c) for variable acoustics, B for bathymetry.
+int aux_planes(int system) {
+    return system == CLAW_ACOUSTICS_VAR ? 2 : (system == CLAW_SHALLOW_WATER_BATHY ? 1 : 0);
 }
 
 }  // namespace
@@ -393,9 +400,9 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
     const CUtensorMapSwizzle xsw = cx * es == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
     const cuuint32_t ct = (cuuint32_t)(32 / es);   // cells per chunk along y / z (4 KB boxes)
     for (int kind = 0; kind < 2; ++kind) {
-        if (kind == 1 && s->system != CLAW_ACOUSTICS_VAR) break;
+        if (kind == 1 && aux_planes(s->system) == 0) break;
         char* base = kind == 0 ? (char*)s->pool + I.offset * es : (char*)s->aux + I.aux_offset * es;
-        const cuuint64_t planes = kind == 0 ? 3 * (cuuint64_t)s->m : 2;
+        const cuuint64_t planes = kind == 0 ? 3 * (cuuint64_t)s->m : (cuuint64_t)aux_planes(s->system);
         {
             const cuuint64_t dims[3] = {(cuuint64_t)I.n[0], (cuuint64_t)I.n[1] * I.n[2], planes};
             const cuuint64_t str[2] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.fstride * es};
@@ -437,13 +444,13 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     *out = nullptr;
     if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
     if (!grids || !bc || !params) return fail(CLAW_EINVAL, "NULL argument");
-    if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
+    if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER_BATHY) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
     if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_FIRST_ORDER) return fail(CLAW_EINVAL, "unknown limiter %d", (int)limiter);
     const int ndim = grids[0].ndim;
     for (int i = 0; i < B; ++i) CKS(check_grid(&grids[i], ndim));
-    if (system == CLAW_SHALLOW_WATER && ndim != 2) return fail(CLAW_EINVAL, "shallow water is 2D only");
-    const int m_exp = system == CLAW_SHALLOW_WATER ? 3 : ndim + 1;
-    const int mw_exp = system == CLAW_SHALLOW_WATER ? 3 : 2;
+    if (is_sw(system) && ndim != 2) return fail(CLAW_EINVAL, "shallow water is 2D only");
+    const int m_exp = is_sw(system) ? 3 : ndim + 1;
+    const int mw_exp = is_sw(system) ? 3 : 2;
     if (m != m_exp || mwaves != mw_exp)
         return fail(CLAW_EINVAL, "(m, mwaves) = (%d, %d) does not match the system (expected (%d, %d))", m, mwaves, m_exp, mw_exp);
     for (int k = 0; k < 2 * ndim; ++k)
@@ -453,9 +460,9 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
         return fail(CLAW_EINVAL, "unknown splitting %d", params->splitting);
     if (!(params->cfl_desired > 0.0) || !(params->cfl_max > 0.0)) return fail(CLAW_EINVAL, "cfl_desired and cfl_max must be > 0");
     if (!(params->dt_max > 0.0)) return fail(CLAW_EINVAL, "dt_max must be > 0");
-    if (system != CLAW_SHALLOW_WATER && (!(params->rho > 0.0) || !(params->K > 0.0)))
+    if (!is_sw(system) && (!(params->rho > 0.0) || !(params->K > 0.0)))
         return fail(CLAW_EINVAL, "rho and K must be > 0");
-    if (system == CLAW_SHALLOW_WATER && !(params->g > 0.0)) return fail(CLAW_EINVAL, "g must be > 0");
+    if (is_sw(system) && !(params->g > 0.0)) return fail(CLAW_EINVAL, "g must be > 0");
 
     claw_solver* s = new claw_solver();
     s->B = B;
@@ -502,9 +509,9 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
         I.offset = off;
         off += 3 * I.vstride;
         off = (off + 63) / 64 * 64;
-        if (system == CLAW_ACOUSTICS_VAR) {
+        if (aux_planes(system) > 0) {
             I.aux_offset = aux_off;
-            aux_off += 2 * I.fstride;
+            aux_off += aux_planes(system) * I.fstride;
             aux_off = (aux_off + 63) / 64 * 64;
         } else {
             I.aux_offset = -1;
@@ -514,7 +521,10 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     }
     CK(cudaMalloc(&s->pool, (size_t)off * s->esize));
     CK(cudaMemsetAsync(s->pool, 0, (size_t)off * s->esize, s->stream));
-    if (aux_off) CK(cudaMalloc(&s->aux, (size_t)aux_off * s->esize));
+    if (aux_off) {
+        CK(cudaMalloc(&s->aux, (size_t)aux_off * s->esize));
+        CK(cudaMemsetAsync(s->aux, 0, (size_t)aux_off * s->esize, s->stream));   // flat bottom
+    }
     s->stage_elems = max_cells * m;
     CK(cudaMalloc(&s->stage, s->stage_elems * sizeof(double)));
     CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
@@ -583,7 +593,7 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     CKS(build_tiles(s));
     // Initial state: zero (h = 1 for shallow water); material from params.
     for (int i = 0; i < B; ++i) {
-        if (system == CLAW_SHALLOW_WATER) CK(launch_fill(s->precision, s->pool, s->inst[i], 0, 0, 1.0, s->stream));
+        if (is_sw(system)) CK(launch_fill(s->precision, s->pool, s->inst[i], 0, 0, 1.0, s->stream));
         if (system == CLAW_ACOUSTICS_VAR)
             CK(launch_aux_const(s->precision, s->aux, s->inst[i], params->rho, params->K, s->stream));
         CKS(speed_pass(s, i, 1));
@@ -647,6 +657,23 @@ claw_status set_aux_impl(claw_solver* s, int i, const double* rho, const double*
     return CLAW_OK;
 }
 
+claw_status set_bathymetry_impl(claw_solver* s, int i, const double* B, int on_device) {
+    CKS(check_solver(s, i));
+    if (s->system != CLAW_SHALLOW_WATER_BATHY)
+        return fail(CLAW_EINVAL, "claw_set_bathymetry needs CLAW_SHALLOW_WATER_BATHY");
+    if (!B) return fail(CLAW_EINVAL, "B is NULL");
+    const InstDesc& I = s->inst[i];
+    const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2];
+    const double* b = B;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(s->stage, B, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        b = s->stage;
+    }
+    CK(launch_aux_plane(s->precision, s->aux, I, 0, b, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CLAW_OK;
+}
+
 }  // namespace
 
 void claw::set_last_error(const char* msg) { g_err = msg; }
@@ -657,6 +684,9 @@ cudaError_t claw::launch_sweep(const SweepLaunch& L) {
             return L.precision == 64 ? launch_sweep_acoustics_f64(L) : launch_sweep_acoustics_f32(L);
         case kSysAcousticsVar:
             return L.precision == 64 ? launch_sweep_acoustics_var_f64(L) : launch_sweep_acoustics_var_f32(L);
+        case kSysShallowWaterBathy:
+            return L.precision == 64 ? launch_sweep_shallow_water_bathy_f64(L)
+                                     : launch_sweep_shallow_water_bathy_f32(L);
         default:
             return L.precision == 64 ? launch_sweep_shallow_water_f64(L) : launch_sweep_shallow_water_f32(L);
     }
@@ -685,8 +715,8 @@ claw_status claw_ensemble_create(int B, const claw_grid* grids, claw_system syst
     if (!grids) return fail(CLAW_EINVAL, "grids is NULL");
     if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
     const int ndim = grids[0].ndim;
-    const int m = system == CLAW_SHALLOW_WATER ? 3 : ndim + 1;
-    const int mw = system == CLAW_SHALLOW_WATER ? 3 : 2;
+    const int m = is_sw(system) ? 3 : ndim + 1;
+    const int mw = is_sw(system) ? 3 : 2;
     claw_status st = create_impl(B, grids, m, mw, system, limiter, bc, params, cuda_stream, out);
     if (st != CLAW_OK && out && *out) {
         std::string keep = g_err;
@@ -731,6 +761,12 @@ claw_status claw_ensemble_get_q(claw_solver* s, int i, double* q, int on_device)
 }
 claw_status claw_ensemble_set_aux(claw_solver* s, int i, const double* rho, const double* K, int on_device) {
     return set_aux_impl(s, i, rho, K, on_device);
+}
+claw_status claw_set_bathymetry(claw_solver* s, const double* B, int on_device) {
+    return set_bathymetry_impl(s, 0, B, on_device);
+}
+claw_status claw_ensemble_set_bathymetry(claw_solver* s, int i, const double* B, int on_device) {
+    return set_bathymetry_impl(s, i, B, on_device);
 }
 int claw_ensemble_size(const claw_solver* s) { return s ? s->B : 0; }
 

@@ -247,6 +247,17 @@ __global__ void aux_kernel(Real* aux, InstDesc I, const double* rho, const doubl
 }
 
 template <class Real>
+__global__ void aux_plane_kernel(Real* aux, InstDesc I, int k, const double* src) {
+    const long long nx = I.n[0];
+    const long long ncell = nx * I.n[1] * I.n[2];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long row = idx / nx, x = idx - row * nx;
+        aux[I.aux_offset + k * I.fstride + row * I.pitch + x] = (Real)src[idx];
+    }
+}
+
+template <class Real>
 __global__ void aux_const_kernel(Real* aux, InstDesc I, double rho, double K) {
     const long long nx = I.n[0];
     const long long ncell = nx * I.n[1] * I.n[2];
@@ -335,6 +346,15 @@ cudaError_t launch_aux_const(int precision, void* aux, const InstDesc& I, double
         aux_const_kernel<double><<<grid_for(I), 256, 0, st>>>((double*)aux, I, rho, K);
     else
         aux_const_kernel<float><<<grid_for(I), 256, 0, st>>>((float*)aux, I, rho, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aux_plane(int precision, void* aux, const InstDesc& I, int k, const double* src,
+                             cudaStream_t st) {
+    if (precision == 64)
+        aux_plane_kernel<double><<<grid_for(I), 256, 0, st>>>((double*)aux, I, k, src);
+    else
+        aux_plane_kernel<float><<<grid_for(I), 256, 0, st>>>((float*)aux, I, k, src);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 
 namespace claw {
 
-enum : int { kSysAcoustics = 0, kSysAcousticsVar = 1, kSysShallowWater = 2 };
+enum : int { kSysAcoustics = 0, kSysAcousticsVar = 1, kSysShallowWater = 2, kSysShallowWaterBathy = 3 };
 
 struct SweepLaunch {
     SweepArgs args;
@@ -32,6 +32,8 @@ cudaError_t launch_sweep_acoustics_var_f32(const SweepLaunch& L);
 cudaError_t launch_sweep_acoustics_var_f64(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_f32(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_f64(const SweepLaunch& L);
+cudaError_t launch_sweep_shallow_water_bathy_f32(const SweepLaunch& L);
+cudaError_t launch_sweep_shallow_water_bathy_f64(const SweepLaunch& L);
 
 struct FinalSlots {
     int off[4];      // slot offset of each field's result after a full step
@@ -59,6 +61,9 @@ cudaError_t launch_fill(int precision, void* pool, const InstDesc& I, int slot, 
 cudaError_t launch_aux(int precision, void* aux, const InstDesc& I, const double* rho,
                        const double* K, cudaStream_t st);
 cudaError_t launch_aux_const(int precision, void* aux, const InstDesc& I, double rho, double K,
+                             cudaStream_t st);
+// One material plane (FP64 values, x fastest, no padding) into plane k.
+cudaError_t launch_aux_plane(int precision, void* aux, const InstDesc& I, int k, const double* src,
                              cudaStream_t st);
 cudaError_t launch_sums(int precision, const void* pool, const InstDesc& I, const Control* ctl,
                         int m, double* out, cudaStream_t st);

@@ -14,6 +14,9 @@
 //   prepare(cell, P)   fill the precomputed part of a freshly loaded cell
 //   solve(l, r, P, w)  waves w.W[p][c], speeds w.s[p], fluctuations
 //                      w.amdq[c] (A-dQ), w.apdq[c] (A+dQ)
+//   set_aux(cell, a)   store the cell's material values a[0..NA-1]
+//   kFWave             true when solve() returns f-waves Z_p (the source
+//                      folded in); the correction then weighs by sign(s_p)
 //   nonphysical(q)     true for a state the method cannot continue from
 //   zero(p, c)         true where component c of wave p is identically zero
 //                      (products with it are skipped: IEEE rules forbid the
@@ -102,6 +105,13 @@ struct Acoustics {
     __device__ __forceinline__ static int field(int d, int comp) { return comp == 0 ? 0 : 1 + d; }
     __host__ __device__ static constexpr bool zero(int, int) { return false; }
 
+    static constexpr bool kFWave = false;
+
+    __device__ __forceinline__ static void set_aux(Cell& cell, const Real* a) {
+        cell.Z = a[0];
+        cell.c = a[1];
+    }
+
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
         if (!VAR) {
             cell.Z = P.Z;
@@ -177,12 +187,14 @@ struct ShallowWater {
         Real c;      // sqrt(g h)
     };
     static constexpr bool kFast = !std::is_same<Real, double>::value;
+    static constexpr bool kFWave = false;
 
     __device__ __forceinline__ static int field(int d, int comp) {
         return comp == 0 ? 0 : (comp == 1 ? 1 + d : 2 - d);
     }
     // the shear wave W2 = (0, 0, alpha2)
     __host__ __device__ static constexpr bool zero(int p, int c) { return p == 1 && c < 2; }
+    __device__ __forceinline__ static void set_aux(Cell&, const Real*) {}
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
         if constexpr (kFast) {
@@ -203,7 +215,8 @@ struct ShallowWater {
     }
 
     // Roe averages; i2c = 1 / (2 c_hat), ni2c = -i2c.
-    __device__ __forceinline__ static void roe(const Cell& l, const Cell& r, const Params& P,
+    template <class C>
+    __device__ __forceinline__ static void roe(const C& l, const C& r, const Params& P,
                                                Real& uh, Real& vh, Real& ch, Real& i2c, Real& ni2c) {
         const Real den = Ops<Real>::rcp(l.sqh + r.sqh);
         uh = vfma(l.sqh, l.u, r.sqh * r.u) * den;
@@ -310,6 +323,117 @@ struct ShallowWater {
     // signed-integer minimum; a minimum <= 0 means some h <= 0 (a NaN h
     // makes the next sweep's speeds NaN, caught there).
     static constexpr bool kMinH = true;
+};
+
+// ------------------------------------------------------------------------
+// Shallow water over a bottom elevation B (one material value per cell): the
+// source (0, -g h B_x, -g h B_y) of the Clawpack base of Sec. 3 folded into
+// the Riemann problem as f-waves (well-balanced):
+//   delta = f(Q_r) - f(Q_l) - psi,  psi = (0, -g h_bar (B_r - B_l), 0),
+//   delta_0 = d(hu),  delta_1 = d(hu u) + g h_bar (dh + dB),  delta_2 = d(hu v)
+// (g (h_r^2 - h_l^2)/2 = g h_bar dh, so a lake at rest gives delta = 0
+// exactly), split on the Roe eigenvectors: Z_p = beta_p r_p with
+//   beta_1 = (s3 delta_0 - delta_1) / 2c,  beta_2 = delta_2 - v_hat delta_0,
+//   beta_3 = (delta_1 - s1 delta_0) / 2c.
+// A-dQ sums the Z_p with s_p < 0, A+dQ the others.  No entropy fix.  The
+// negated differences below are exact negations, so the strengths need no
+// negated operands.
+// ------------------------------------------------------------------------
+template <class Real>   // double, float, or f2 (two lines)
+struct ShallowWaterBathy {
+    using Value = Real;
+    using SW = ShallowWater<Real>;
+    static constexpr int NQ = 3;
+    static constexpr int NW = 3;
+    static constexpr int NA = 1;
+    using Params = typename SW::Params;
+    struct Cell {
+        Real q[NQ];
+        Real u, v, sqh, c;
+        Real fu, fv;   // hu u, hu v (normal flux terms)
+        Real B;        // bottom elevation
+    };
+    static constexpr bool kFWave = true;
+    static constexpr bool kMinH = true;
+
+    __device__ __forceinline__ static int field(int d, int comp) { return SW::field(d, comp); }
+    __host__ __device__ static constexpr bool zero(int p, int c) { return p == 1 && c < 2; }
+    __device__ __forceinline__ static void set_aux(Cell& cell, const Real* a) { cell.B = a[0]; }
+
+    __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
+        if constexpr (SW::kFast) {
+            const Real r = Ops<Real>::rsqrt(cell.q[0]);
+            const Real rh = r * r;
+            cell.sqh = cell.q[0] * r;
+            cell.u = cell.q[1] * rh;
+            cell.v = cell.q[2] * rh;
+            cell.c = P.sqrt_g * cell.sqh;
+        } else {
+            const Real rh = Real(1) / cell.q[0];
+            cell.u = cell.q[1] * rh;
+            cell.v = cell.q[2] * rh;
+            cell.sqh = sqrt(cell.q[0]);
+            cell.c = sqrt(P.g * cell.q[0]);
+        }
+        cell.fu = cell.q[1] * cell.u;
+        cell.fv = cell.q[1] * cell.v;
+    }
+
+    __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
+                                                 Waves<Real, NQ, NW>& w) {
+        Real uh, vh, ch, i2c, ni2c;
+        SW::roe(l, r, P, uh, vh, ch, i2c, ni2c);
+        const Real s1 = uh - ch, s3 = uh + ch;
+        const Real d0 = r.q[1] - l.q[1];
+        const Real nd0 = l.q[1] - r.q[1];
+        const Real d2 = r.fv - l.fv;
+        // -delta_1 = (fu_l - fu_r) + g h_bar ((h_l - h_r) + (B_l - B_r))
+        const Real ghb = P.half_g * (l.q[0] + r.q[0]);
+        const Real nd1 = vfma(ghb, (l.q[0] - r.q[0]) + (l.B - r.B), l.fu - r.fu);
+        const Real b1 = vfma(s3, d0, nd1) * i2c;
+        const Real b2 = vfma(vh, nd0, d2);
+        const Real b3 = vfma(s1, d0, nd1) * ni2c;
+        w.s[0] = s1;
+        w.s[1] = uh;
+        w.s[2] = s3;
+        w.W[0][0] = b1;
+        w.W[0][1] = b1 * s1;
+        w.W[0][2] = b1 * vh;
+        w.W[1][0] = Real(0);
+        w.W[1][1] = Real(0);
+        w.W[1][2] = b2;
+        w.W[2][0] = b3;
+        w.W[2][1] = b3 * s3;
+        w.W[2][2] = b3 * vh;
+        const auto n0 = vlt(s1, Real(0)), n1 = vlt(uh, Real(0)), n2 = vlt(s3, Real(0));
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            Real am = Real(0), ap = Real(0);
+            if (!zero(0, c)) {
+                am = am + sel(n0, w.W[0][c], Real(0));
+                ap = ap + sel(n0, Real(0), w.W[0][c]);
+            }
+            if (!zero(1, c)) {
+                am = am + sel(n1, w.W[1][c], Real(0));
+                ap = ap + sel(n1, Real(0), w.W[1][c]);
+            }
+            am = am + sel(n2, w.W[2][c], Real(0));
+            ap = ap + sel(n2, Real(0), w.W[2][c]);
+            w.amdq[c] = am;
+            w.apdq[c] = ap;
+        }
+    }
+
+    __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params& P,
+                                                  Real s[NW]) {
+        Real uh, vh, ch, i2c, ni2c;
+        SW::roe(l, r, P, uh, vh, ch, i2c, ni2c);
+        s[0] = uh - ch;
+        s[1] = uh;
+        s[2] = uh + ch;
+    }
+    __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) { return SW::max_speed(w); }
+    __device__ __forceinline__ static auto nonphysical(const Real q[NQ]) { return SW::nonphysical(q); }
 };
 
 // ------------------------------------------------------------------------

@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
         for (int c = 0; c < NQ; ++c) cell.q[c] = __ldg(qin[c] + o);
         if (flip) cell.q[1] = -cell.q[1];
         if constexpr (Sys::NA > 0) {
-            cell.Z = __ldg(aux + o);
-            cell.c = __ldg(aux + I.fstride + o);
+            Real a[Sys::NA];
+#pragma unroll
+            for (int k = 0; k < Sys::NA; ++k) a[k] = __ldg(aux + k * I.fstride + o);
+            Sys::set_aux(cell, a);
         }
         Sys::prepare(cell, P);
     };
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
     auto load_direct = [&](int kc, Cell& cell) {
         bool flip;
         const int j = map_cell(kc, N, bc_lo, bc_hi, flip);
+        V a[NA > 0 ? NA : 1];
 #pragma unroll
         for (int k = 0; k < PK; ++k) {
             const long long o = base[k] + (long long)j * stride;
@@ -318,11 +321,11 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
                 if (c == 1 && flip) x = -x;
                 set_lane(cell.q[c], k, x);
             }
-            if constexpr (NA > 0) {
-                set_lane(cell.Z, k, valid[k] ? __ldg(aux + o) : Real(1));
-                set_lane(cell.c, k, valid[k] ? __ldg(aux + I.fstride + o) : Real(1));
-            }
+#pragma unroll
+            for (int m = 0; m < NA; ++m)
+                set_lane(a[m], k, valid[k] ? __ldg(aux + m * I.fstride + o) : Real(1));
         }
+        if constexpr (NA > 0) Sys::set_aux(cell, a);
         Sys::prepare(cell, P);
     };
 
@@ -368,7 +371,12 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
                 phi = limiter_ratio<LIM, V>(num, ssB[p]);
             }
             const V as = vabs(sp);
-            const V k = V(0.5f) * as * vfma(nnu, as, V(1)) * phi;   // 1/2 |s| (1 - nu |s|) phi
+            // 1/2 |s| (1 - nu |s|) phi; f-waves Z = s W: 1/2 sign(s) (1 - nu |s|) phi
+            V k;
+            if constexpr (Sys::kFWave)
+                k = sel(vgt(sp, V(0)), V(0.5f), sel(vlt(sp, V(0)), V(-0.5f), V(0))) * vfma(nnu, as, V(1)) * phi;
+            else
+                k = V(0.5f) * as * vfma(nnu, as, V(1)) * phi;
 #pragma unroll
             for (int c = 0; c < NQ; ++c)
                 if (!Sys::zero(p, c)) F[c] = vfma(k, wB.W[p][c], F[c]);
@@ -539,10 +547,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
         auto make_cell = [&](const V* vals, Cell& cur) {
 #pragma unroll
             for (int c = 0; c < NQ; ++c) cur.q[c] = vals[c];
-            if constexpr (NA > 0) {
-                cur.Z = vals[NQ];
-                cur.c = vals[NQ + 1];
-            }
+            if constexpr (NA > 0) Sys::set_aux(cur, vals + NQ);
             Sys::prepare(cur, P);
         };
         // One cell of line `lane` at a time.  x sweep: the result of cell

@@ -10,7 +10,7 @@ from . import _lib as L
 
 
 def _nm(system: str, ndim: int):
-    return (3, 3) if system == "shallow_water" else (ndim + 1, 2)
+    return (3, 3) if system.startswith("shallow_water") else (ndim + 1, 2)
 
 
 class Solver:
@@ -37,6 +37,8 @@ class Solver:
                 cfl_max=prob.cfl_max, stream=stream, **kw)
         if prob.system == "acoustics_var":
             s.set_aux(prob.rho_cell, prob.K_cell)
+        if prob.system == "shallow_water_bathy" and prob.B_cell is not None:
+            s.set_bathymetry(prob.B_cell)
         s.set_q(prob.q0)
         return s
 
@@ -69,6 +71,9 @@ class Solver:
 
     def set_aux(self, rho, K):
         L.claw_set_aux(self.h, rho, K)
+
+    def set_bathymetry(self, B):
+        L.claw_set_bathymetry(self.h, B)
 
     def step(self, dt=0.0):
         return L.claw_step(self.h, dt)
@@ -128,6 +133,8 @@ class Ensemble:
         for i, p in enumerate(probs):
             if p.system == "acoustics_var":
                 e.set_aux(i, p.rho_cell, p.K_cell)
+            if p.system == "shallow_water_bathy" and p.B_cell is not None:
+                e.set_bathymetry(i, p.B_cell)
             e.set_q(i, p.q0)
         return e
 
@@ -158,6 +165,9 @@ class Ensemble:
 
     def set_aux(self, i, rho, K):
         L.claw_ensemble_set_aux(self.h, i, rho, K)
+
+    def set_bathymetry(self, i, B):
+        L.claw_ensemble_set_bathymetry(self.h, i, B)
 
     def run_steps(self, nsteps):
         L.claw_ensemble_run_steps(self.h, nsteps)

@@ -112,6 +112,22 @@ def test_layers_512_100_steps_fp32_vs_fp64_and_symmetry(layers):
     assert np.abs(q64[1] + q64[1][:, :, ::-1]).max() <= 1e-12 * scale
 
 
+def test_seamount_4096_against_oracle():
+    """Shallow water over a seamount at 4096^2 (the bathymetry benchmark
+    workload): 20 steps, FP64 against the oracle to 1e-12, FP32 to 1e-4 on h
+    and 1e-3 on the surface perturbation h + B - 1."""
+    prob = inputs.sw_bathymetry(4096)
+    ref = Oracle(prob).run_steps(prob.q0, 20)
+    q64, (t, dt, n) = gpu_run(prob, 20, 64, autotune=False)
+    assert n == 20
+    assert fieldwise_linf(q64, ref["q"]) <= TOL64
+    assert t == pytest.approx(ref["t"], rel=1e-13)
+    q32, _ = gpu_run(prob, 20, 32)
+    assert oracle.rel_l1(q32[0], ref["q"][0]) <= 1e-4
+    eta, eta_ref = q32[0] + prob.B_cell - 1.0, ref["q"][0] + prob.B_cell - 1.0
+    assert oracle.rel_l1(eta, eta_ref) <= 1e-3
+
+
 SW_SAMPLE = [0, 1, 2, 3, 64, 128, 200, 255]
 
 

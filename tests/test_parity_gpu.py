@@ -74,6 +74,11 @@ CASES += [("acoustics", (130, 67), "mc", ("wall", "extrap", "periodic", "wall"))
           ("acoustics", (129, 11), "minmod", "wall"),
           ("shallow_water", (2, 5), "minmod", "wall"),
           ("acoustics_var", (3, 2, 2), "mc", "periodic"),
+          # shallow water over bathymetry (f-waves)
+          ("shallow_water_bathy", (37, 29), "minmod", "periodic"),
+          ("shallow_water_bathy", (37, 29), "mc", "wall"),
+          ("shallow_water_bathy", (131, 67), "none", "extrap"),
+          ("shallow_water_bathy", (73, 20), "first_order", ("periodic", "periodic", "wall", "extrap")),
           # first-order method (no correction term)
           ("acoustics", (37, 29), "first_order", "wall"),
           ("shallow_water", (131, 67), "first_order", "extrap"),
@@ -308,6 +313,38 @@ def test_strang_ensemble_matches_oracle_per_instance():
         assert fieldwise_linf(e.get_q(i), ref["q"]) <= TOL64
         assert e.time(i)[0] == pytest.approx(ref["t"], rel=1e-14)
     e.close()
+
+
+# ------------------------------------------------------------ bathymetry
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("bc", ["periodic", "extrap", "wall"])
+def test_bathymetry_lake_at_rest_bitwise(precision, bc):
+    """A flat surface at rest over a seamount stays exactly at rest in both
+    precisions (B and h are multiples of 2^-24, exact in FP32 too)."""
+    prob = inputs.sw_bathymetry(96, limiter="mc", bc=bc, hump=0.0)
+    with Solver.from_problem(prob, precision=precision) as s:
+        s.run_steps(10)
+        q = s.get_q()
+    np.testing.assert_array_equal(q, prob.q0)
+
+
+def test_bathymetry_ensemble_matches_oracle_per_instance():
+    probs = [inputs.random_problem("shallow_water_bathy", (n, n + 3), "minmod", "periodic", seed=s)
+             for s, n in ((1, 24), (2, 57), (3, 40))]
+    e = Ensemble.from_problems(probs, precision=64)
+    e.run_steps(8)
+    for i, p in enumerate(probs):
+        ref = Oracle(p).run_steps(p.q0, 8)
+        assert fieldwise_linf(e.get_q(i), ref["q"]) <= TOL64
+    e.close()
+
+
+def test_set_bathymetry_rejects_other_systems():
+    prob = inputs.random_problem("shallow_water", (16, 16), "minmod", "periodic")
+    with Solver.from_problem(prob) as s:
+        with pytest.raises(ClawError):
+            s.set_bathymetry(np.zeros((16, 16)))
 
 
 # ------------------------------------------------------------------ ensembles
