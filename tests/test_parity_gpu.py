@@ -285,7 +285,8 @@ STRANG_CASES = [("shallow_water", (45, 38), "minmod", "periodic"),
                 ("shallow_water", (64, 33), "mc", ("extrap", "wall", "wall", "extrap")),
                 ("acoustics", (37, 29), "mc", "wall"),
                 ("acoustics_var", (23, 19, 21), "mc", ("periodic", "periodic", "wall", "wall", "extrap", "extrap")),
-                ("acoustics", (17, 21, 25), "first_order", "periodic")]
+                ("acoustics", (17, 21, 25), "first_order", "periodic"),
+                ("shallow_water_bathy", (44, 31), "mc", ("periodic", "periodic", "wall", "extrap"))]
 
 
 @pytest.mark.parametrize("system,shape,limiter,bc", STRANG_CASES)
