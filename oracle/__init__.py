@@ -21,7 +21,7 @@ from . import build as _build
 _SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3}
 _LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 _BCS = {"periodic": 0, "extrap": 1, "wall": 2}
-_SPLITTINGS = {"godunov": 0, "strang": 1}
+_SPLITTINGS = {"godunov": 0, "strang": 1, "unsplit": 2}
 
 _dp = C.POINTER(C.c_double)
 
@@ -68,6 +68,10 @@ def lib():
         L.orc_rp_shallow_water_bathy.restype = None
         L.orc_rp_shallow_water_bathy.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
                                                  _dp, _dp, _dp, _dp]
+        L.orc_tr_acoustics.restype = None
+        L.orc_tr_acoustics.argtypes = [_dp] + [C.c_double] * 6 + [_dp, _dp]
+        L.orc_tr_shallow_water.restype = None
+        L.orc_tr_shallow_water.argtypes = [_dp, _dp, _dp, _dp, C.c_double, _dp, _dp]
         L.orc_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -145,6 +149,8 @@ class Oracle:
         st = lib().orc_run(C.byref(self.P), _ptr(q), mode, int(nsteps), float(t_final),
                            float(fixed_dt), C.byref(t_), C.byref(dt_), C.byref(nacc),
                            C.byref(nrej), C.byref(cfl))
+        if st == -2:
+            raise ValueError("the unsplit update covers 2D acoustics and shallow water only")
         return dict(q=q, t=t_.value, dt=dt_.value, nacc=nacc.value, nrej=nrej.value,
                     cfl=cfl.value, status=st)
 
@@ -179,6 +185,21 @@ def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81,
     lib().orc_rp_acoustics(_ptr(ql), _ptr(qr), float(rho_l), float(K_l), float(rho_r),
                            float(K_r), _ptr(W), _ptr(s), _ptr(am), _ptr(ap))
     return W[:2, :2], s[:2], am[:2], ap[:2]
+
+
+def transverse(system: str, a, qd=None, qc=None, qu=None, rho=(1.0, 1.0, 1.0), K=(1.0, 1.0, 1.0),
+               g=9.81):
+    """Transverse split of a reduced fluctuation a (cell below d, cell c,
+    cell above u): the parts crossing the lower and upper interfaces."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    bm, bp = np.zeros(3), np.zeros(3)
+    if system == "shallow_water":
+        qd, qc, qu = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (qd, qc, qu))
+        lib().orc_tr_shallow_water(_ptr(a), _ptr(qd), _ptr(qc), _ptr(qu), float(g), _ptr(bm), _ptr(bp))
+    else:
+        lib().orc_tr_acoustics(_ptr(a), float(rho[0]), float(K[0]), float(rho[1]), float(K[1]),
+                               float(rho[2]), float(K[2]), _ptr(bm), _ptr(bp))
+    return bm, bp
 
 
 def phi(limiter: str, theta: float) -> float:

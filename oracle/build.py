@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["orc_acoustics.c", "orc_shallow_water.c", "orc_wavesweep.c"]
+SOURCES = ["orc_acoustics.c", "orc_shallow_water.c", "orc_wavesweep.c", "orc_unsplit.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liborc.so")
 

@@ -42,8 +42,9 @@ enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_MC = 2, ORC_LIM_FIRST_ORDER
 enum { ORC_BC_PERIODIC = 0, ORC_BC_EXTRAP = 1, ORC_BC_WALL = 2 };
 /* Sweep order of a step (the splittings of Eq. LW-update's Clawpack base,
  * Sec. 3): GODUNOV x(dt) y(dt) [z(dt)]; STRANG x(dt/2) y(dt) x(dt/2) in 2D,
- * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D. */
-enum { ORC_SPLIT_GODUNOV = 0, ORC_SPLIT_STRANG = 1 };
+ * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D; UNSPLIT one update from the x
+ * and y Riemann problems of Q^n with transverse waves (2D; orc_unsplit.c). */
+enum { ORC_SPLIT_GODUNOV = 0, ORC_SPLIT_STRANG = 1, ORC_SPLIT_UNSPLIT = 2 };
 
 typedef struct {
     int ndim;              /* 2 or 3 */
@@ -91,6 +92,21 @@ double orc_phi(int limiter, double theta);
 double orc_sweep(const orc_problem *P, int d, const double *qin, double *qout,
                  double dt, long line_lo, long line_hi);
 
+/* Transverse solvers of the unsplit update (see orc_unsplit.c): split the
+ * reduced fluctuation a (p or h, normal, transverse component) of a cell
+ * into the parts crossing its lower (bm) and upper (bp) transverse
+ * interfaces. */
+void orc_tr_acoustics(const double *a, double rho_d, double K_d, double rho_c, double K_c,
+                      double rho_u, double K_u, double bm[3], double bp[3]);
+void orc_tr_shallow_water(const double *a, const double *qd, const double *qc,
+                          const double *qu, double g, double bm[3], double bp[3]);
+
+/* One unsplit step qin -> qout with dt (2D acoustics or shallow water);
+ * m_d[0], m_d[1] receive the largest |s| along x and y.  Returns 0, or -1
+ * for a problem it does not cover. */
+int orc_unsplit_step(const orc_problem *P, const double *qin, double *qout, double dt,
+                     double m_d[3]);
+
 /* Largest |s^p| along direction d from a Riemann pass over q (no update). */
 double orc_max_speed_dir(const orc_problem *P, int d, const double *q);
 
@@ -108,7 +124,8 @@ int orc_sequence(const orc_problem *P, int dirs[5], double frac[5]);
  *   *dt <= 0 on entry: start from dt = cfl_desired / max_d(m_d / dx_d) of q.
  *   fixed_dt > 0: every step uses fixed_dt and is accepted (no CFL control).
  * On return q holds the new state, *t, *dt (the next step), *nacc, *nrej
- * are updated.  Returns 0, or -1 after max_retries consecutive rejections. */
+ * are updated.  Returns 0, -1 after max_retries consecutive rejections, or
+ * -2 for an unsplit step on a problem it does not cover. */
 int orc_run(const orc_problem *P, double *q, int mode, long nsteps, double t_final,
             double fixed_dt, double *t, double *dt, long *nacc, long *nrej,
             double *cfl_last);

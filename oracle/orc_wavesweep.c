@@ -407,15 +407,20 @@ int orc_run(const orc_problem *P, double *q, int mode, long nsteps, double t_fin
         double m_d[3] = {0.0, 0.0, 0.0};
         const double *src = q;
         double *dst = a;
-        int dirs[5];
-        double frac[5];
-        int nsw = orc_sequence(P, dirs, frac);
         for (int d = 0; d < 3; ++d) m_d[d] = 0.0;
-        for (int k = 0; k < nsw; ++k) {
-            double m = orc_sweep(P, dirs[k], src, dst, frac[k] * dt_try, 0, -1);
-            if (m > m_d[dirs[k]]) m_d[dirs[k]] = m;
-            src = dst;
-            dst = (dst == a) ? b : a;
+        if (P->splitting == ORC_SPLIT_UNSPLIT) {
+            if (orc_unsplit_step(P, q, a, dt_try, m_d) != 0) { status = -2; break; }
+            src = a;
+        } else {
+            int dirs[5];
+            double frac[5];
+            int nsw = orc_sequence(P, dirs, frac);
+            for (int k = 0; k < nsw; ++k) {
+                double m = orc_sweep(P, dirs[k], src, dst, frac[k] * dt_try, 0, -1);
+                if (m > m_d[dirs[k]]) m_d[dirs[k]] = m;
+                src = dst;
+                dst = (dst == a) ? b : a;
+            }
         }
         double M = speed_over_dx(P, m_d);
         double cfl = dt_try * M;

@@ -26,7 +26,7 @@ SEED = 1805
 SYSTEMS = ("acoustics", "acoustics_var", "shallow_water", "shallow_water_bathy")
 LIMITERS = ("none", "minmod", "mc", "first_order")
 BCS = ("periodic", "extrap", "wall")
-SPLITTINGS = ("godunov", "strang")
+SPLITTINGS = ("godunov", "strang", "unsplit")
 
 
 @dataclass

@@ -75,6 +75,18 @@ MUTANTS = [
      "g * h_r * ((h_r - h_l) + (B_r - B_l));", "source depth from one side"),
     ("orc_wavesweep.c", "double k = fwave ? (sp > 0.0 ? 1.0 : (sp < 0.0 ? -1.0 : 0.0)) : as;",
      "double k = as;", "f-wave correction weighted by |s| instead of sign(s)"),
+    ("orc_unsplit.c", "flux_t[3 * kb + c] -= 0.5 * nu[d] * fm[c];\n                        flux_t[3 * ka + c] -= 0.5 * nu[d] * fp[c];",
+     "(void)fm; (void)fp;", "unsplit update without transverse terms"),
+    ("orc_unsplit.c", "flux_t[3 * kb + c] -= 0.5 * nu[d] * fm[c];\n                        flux_t[3 * ka + c] -= 0.5 * nu[d] * fp[c];",
+     "flux_t[3 * kb + c] += 0.5 * nu[d] * fm[c];\n                        flux_t[3 * ka + c] += 0.5 * nu[d] * fp[c];",
+     "transverse terms with the wrong sign"),
+    ("orc_unsplit.c", "double al = (-a[0] + Z_c * a[2]) / (Z_d + Z_c);",
+     "double al = (-a[0] + Z_c * a[2]) / (Z_u + Z_c);", "transverse split with the wrong neighbour's impedance"),
+    ("orc_unsplit.c", "double lam[3] = {vt - ct, vt, vt + ct};",
+     "double lam[3] = {ut - ct, ut, ut + ct};", "transverse speeds from the velocity along the sweep"),
+    ("orc_unsplit.c", "if (I - 1 >= 0) for (int c = 0; c < 3; ++c) fl[3 * (d * np + pidx(&u, il, jl)) + c] += fa[c];",
+     "if (I - 1 >= 0) for (int c = 0; c < 3; ++c) fl[3 * (d * np + pidx(&u, il, jl)) + c] += fb[c];",
+     "left fluctuation taken from the wrong side"),
 ]
 
 

@@ -718,3 +718,176 @@ def test_bathymetry_mass_conservation_periodic():
     p = inputs.random_problem("shallow_water_bathy", (45, 38), "minmod", "periodic", discontinuous=True)
     r = Oracle(p).run_steps(p.q0, 10)["q"]
     assert abs(r[0].sum() - p.q0[0].sum()) <= 1e-13 * p.q0[0].sum()
+
+
+# ---------------------------------------------------------------- unsplit update
+
+def test_transverse_acoustics_sums_to_B_times_fluctuation():
+    """Constant coefficients: the down- and up-going parts add up to B a with
+    B = [[0, 0, K], [0, 0, 0], [1/rho, 0, 0]] on (p, u_n, u_t); the down part
+    moves at -c, the up part at +c along eigenvectors (-+Z, 0, 1)."""
+    rng = np.random.default_rng(61)
+    for rho, K in ((1.0, 4.0), (2.5, 0.7)):
+        B = np.array([[0, 0, K], [0, 0, 0], [1 / rho, 0, 0]])
+        Z = math.sqrt(rho * K)
+        for _ in range(20):
+            a = rng.normal(size=3)
+            bm, bp = oracle.transverse("acoustics", a, rho=(rho,) * 3, K=(K,) * 3)
+            np.testing.assert_allclose(bm + bp, B @ a, rtol=0, atol=1e-14 * (1 + np.abs(B @ a).max()))
+            assert bm[1] == 0.0 and bp[1] == 0.0
+            assert abs(bm[0] + Z * bm[2]) <= 1e-14 * (1 + abs(bm[0]))
+            assert abs(bp[0] - Z * bp[2]) <= 1e-14 * (1 + abs(bp[0]))
+
+
+def test_transverse_shallow_water_sums_to_jacobian_for_equal_states():
+    """With equal states around the cell the Roe averages are that state and
+    the two parts add up to the transverse flux Jacobian (along u_t) applied
+    to a: for g(q) = (h v, h u v, h v^2 + g h^2/2) in (h, h u, h v)."""
+    rng = np.random.default_rng(67)
+    for _ in range(50):
+        h, u, v = rng.uniform(0.3, 3.0), rng.uniform(-1, 1), rng.uniform(-1, 1)
+        q = np.array([h, h * u, h * v])
+        J = np.array([[0.0, 0.0, 1.0],
+                      [-u * v, v, u],
+                      [G * h - v * v, 0.0, 2 * v]])
+        a = rng.normal(size=3)
+        bm, bp = oracle.transverse("shallow_water", a, q, q, q)
+        np.testing.assert_allclose(bm + bp, J @ a, rtol=0, atol=1e-12 * (1 + np.abs(J @ a).max()))
+
+
+@pytest.mark.parametrize("system", ["acoustics", "shallow_water"])
+def test_unsplit_on_y_uniform_data_is_the_1d_scheme(system):
+    """y-uniform periodic data: the y Riemann problems vanish and the
+    transverse fluxes are equal on every row, so the unsplit step equals the
+    split step (whose y sweep does nothing) bitwise."""
+    N, ny = 40, 4
+    rng = np.random.default_rng(71)
+    row = rng.normal(size=(3, N))
+    if system == "shallow_water":
+        row[0] = 1.0 + 0.2 * np.abs(row[0])
+    q0 = np.repeat(row[:, None, :], ny, axis=1)
+    pg = line_problem(system, N, ny=ny, limiter="mc", q0=q0, K=4.0)
+    pu = pg.with_(splitting="unsplit")
+    dt = 0.3 * pg.dx[0] / 4.0
+    np.testing.assert_array_equal(Oracle(pu).run_steps(q0, 3, fixed_dt=dt)["q"],
+                                  Oracle(pg).run_steps(q0, 3, fixed_dt=dt)["q"])
+
+
+@pytest.mark.parametrize("system", ["acoustics", "acoustics_var", "shallow_water"])
+def test_unsplit_commutes_with_transposition(system):
+    """The unsplit update treats x and y alike: transposing the data (and
+    swapping u, v) transposes the result, to rounding -- dimensional
+    splitting does not (its x-then-y order shows at O(dt^2))."""
+    p = inputs.random_problem(system, (24, 24), "mc", "periodic", discontinuous=True)
+    qT = np.stack([p.q0[0].T, p.q0[2].T, p.q0[1].T])
+    pT = p.with_(q0=qT)
+    if system == "acoustics_var":
+        pT = pT.with_(rho_cell=p.rho_cell.T.copy(), K_cell=p.K_cell.T.copy())
+    out = {}
+    for split in ("unsplit", "godunov"):
+        r = Oracle(p.with_(splitting=split)).run_steps(p.q0, 5, fixed_dt=0.002)["q"]
+        rT = Oracle(pT.with_(splitting=split)).run_steps(qT, 5, fixed_dt=0.002)["q"]
+        out[split] = np.abs(r - np.stack([rT[0].T, rT[2].T, rT[1].T])).max()
+    assert out["unsplit"] <= 1e-14
+    assert out["godunov"] >= 1e-4
+
+
+def test_unsplit_diagonal_plane_wave_second_order():
+    """A plane wave along the diagonal (both directions and the transverse
+    terms active): second order without a limiter."""
+    def err(N):
+        c, Z = 2.0, 2.0
+        xs = inputs.centres(N, 0.0, 1.0)
+        Y, X = np.meshgrid(xs, xs, indexing="ij")
+        f = lambda X, Y: np.sin(2 * np.pi * (X + Y))
+        q0 = np.zeros((3, N, N))
+        q0[0] = f(X, Y)
+        q0[1] = q0[0] / (Z * math.sqrt(2))
+        q0[2] = q0[0] / (Z * math.sqrt(2))
+        p = inputs.Problem(2, (N, N), (0, 0), (1, 1), "acoustics", "none", ("periodic",) * 4, q0, K=4.0,
+                           splitting="unsplit")
+        t = 0.125
+        r = Oracle(p).advance(q0, t)
+        s = c * t / math.sqrt(2)
+        return np.abs(r["q"][0] - f(X - s, Y - s)).mean()
+    e = [err(N) for N in (32, 64, 128)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(rates) >= 1.9, (e, rates)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "wall"])
+def test_unsplit_conserves_and_keeps_lake_at_rest(bc):
+    p = inputs.random_problem("shallow_water", (33, 27), "minmod", bc, discontinuous=True).with_(splitting="unsplit")
+    r = Oracle(p).run_steps(p.q0, 8)["q"]
+    assert abs(r[0].sum() - p.q0[0].sum()) <= 1e-13 * p.q0[0].sum()
+    q = np.zeros((3, 27, 33))
+    q[0] = 1.7
+    lake = p.with_(q0=q)
+    np.testing.assert_array_equal(Oracle(lake).run_steps(q, 5)["q"], q)
+
+
+def test_transverse_acoustics_with_different_cells_is_the_normal_solver():
+    """Per-cell coefficients: the down-going part of a fluctuation a is the
+    left-going flux (A-dQ) of the normal Riemann problem between the cell
+    below and the cell for the jump a in (p, u_t), the up-going part the
+    right-going flux (A+dQ) of the problem between the cell and the cell
+    above."""
+    rng = np.random.default_rng(73)
+    for _ in range(30):
+        rho = rng.uniform(0.5, 4.0, size=3)
+        K = rng.uniform(0.5, 4.0, size=3)
+        a = rng.normal(size=3)
+        bm, bp = oracle.transverse("acoustics", a, rho=rho, K=K)
+        jump = [a[0], a[2]]
+        _, _, am_lo, _ = oracle.riemann("acoustics", [0.0, 0.0], jump, rho[0], K[0], rho[1], K[1])
+        _, _, _, ap_hi = oracle.riemann("acoustics", [0.0, 0.0], jump, rho[1], K[1], rho[2], K[2])
+        np.testing.assert_allclose([bm[0], bm[2]], am_lo, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose([bp[0], bp[2]], ap_hi, rtol=1e-13, atol=1e-15)
+        assert bm[1] == 0.0 and bp[1] == 0.0
+
+
+def test_transverse_shallow_water_uses_each_neighbour_for_its_half():
+    """The down-going part depends on the cell below (not above) and the
+    up-going part on the cell above (not below)."""
+    rng = np.random.default_rng(79)
+    def state():
+        h = rng.uniform(0.5, 2.0)
+        return np.array([h, h * rng.uniform(-0.5, 0.5), h * rng.uniform(-0.5, 0.5)])
+    qc, qd, qu, other = state(), state(), state(), state()
+    a = rng.normal(size=3)
+    bm, bp = oracle.transverse("shallow_water", a, qd, qc, qu)
+    bm2, bp2 = oracle.transverse("shallow_water", a, qd, qc, other)
+    bm3, bp3 = oracle.transverse("shallow_water", a, other, qc, qu)
+    np.testing.assert_array_equal(bm, bm2)
+    np.testing.assert_array_equal(bp, bp3)
+    assert np.abs(bp - bp2).max() > 1e-6 and np.abs(bm - bm3).max() > 1e-6
+
+
+def test_unsplit_is_exact_for_quadratic_data():
+    """Constant-coefficient acoustics without a limiter: one unsplit step of
+    cell averages of quadratic data equals the cell averages of the exact
+    solution q0 - t L q0 + t^2/2 L^2 q0 (L = A d/dx + B d/dy; every higher
+    derivative vanishes) away from the boundary -- the transverse waves give
+    the cross term t^2/2 (AB + BA) q_xy.  Dimensional splitting misses it."""
+    rho, K = 1.0, 4.0
+    A = np.array([[0, K, 0], [1 / rho, 0, 0], [0, 0, 0]])
+    B = np.array([[0, 0, K], [0, 0, 0], [1 / rho, 0, 0]])
+    coef = np.random.default_rng(83).normal(size=(3, 6))   # a + b x + c y + d x^2 + e xy + f y^2
+    N = 24
+    dx = 1.0 / N
+    xs = inputs.centres(N, 0.0, 1.0)
+    Y, X = np.meshgrid(xs, xs, indexing="ij")
+    a_, b_, c_, d_, e_, f_ = (coef[:, k][:, None, None] for k in range(6))
+    q0 = a_ + b_ * X + c_ * Y + d_ * X ** 2 + e_ * X * Y + f_ * Y ** 2 + (d_ + f_) * dx ** 2 / 12
+    Px = b_ + 2 * d_ * X + e_ * Y
+    Py = c_ + e_ * X + 2 * f_ * Y
+    Lq = np.einsum("ij,jyx->iyx", A, Px) + np.einsum("ij,jyx->iyx", B, Py)
+    L2q = A @ A @ (2 * coef[:, 3]) + (A @ B + B @ A) @ coef[:, 4] + B @ B @ (2 * coef[:, 5])
+    dt = 0.7 * dx / 2.0
+    exact = q0 - dt * Lq + 0.5 * dt ** 2 * L2q[:, None, None]
+    p = inputs.Problem(2, (N, N), (0, 0), (1, 1), "acoustics", "none", ("extrap",) * 4, q0, K=K,
+                       splitting="unsplit")
+    r = Oracle(p).run_steps(q0, 1, fixed_dt=dt)["q"]
+    assert np.abs(r - exact)[:, 4:-4, 4:-4].max() <= 1e-13 * np.abs(exact).max()
+    rg = Oracle(p.with_(splitting="godunov")).run_steps(q0, 1, fixed_dt=dt)["q"]
+    assert np.abs(rg - exact)[:, 4:-4, 4:-4].max() >= 1e-5
