@@ -216,6 +216,31 @@ def extra_bathymetry(args, peak_gbs):
     return out
 
 
+def extra_unsplit(args, peak_gbs):
+    """The unsplit update with transverse waves on the 4096^2 radial dam
+    break (minmod, outflow): FP32 and FP64 cell-updates/s of the one kernel
+    per step and its HBM fraction (6 values per cell and step: h, hu, hv
+    read once and written once; 24 B in FP32)."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    prob = inputs.sw_radial_dam_break(args.n).with_(splitting="unsplit")
+    out = {"workload": f"2D shallow water radial dam break {args.n}^2, unsplit update with "
+                       f"transverse waves, minmod, outflow, CFL 0.9"}
+    for prec, steps in ((32, 100), (64, 5)):
+        s = Solver.from_problem(prob, precision=prec)
+        seg = s.autotune(2)
+        s.run_steps(3)
+        ms, tot, nl = s.profile_steps(steps)
+        s.close()
+        ach = (6 * prec // 8) * prob.ncells / (ms[0] * 1e-3) / 1e9
+        out[f"f{prec}"] = {"value": prob.ncells * steps / (tot * 1e-3), "ms_per_step": tot / steps,
+                           "kernel_ms": ms[0], "control_ms": ms[3], "steps": steps,
+                           "rows_per_tile": seg[1],
+                           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak_gbs,
+                                        "unit": "GB/s", "frac": ach / peak_gbs,
+                                        "kernel": f"unsplit_kernel<ShallowWater<{'float' if prec == 32 else 'double'}>,minmod>"}}
+    return out
+
+
 # Sec. 7.1 (Tables 1-6): the paper's kernel-analysis problems.  Values a
 # sweep reads and writes per cell (fields it leaves unchanged are neither):
 # 2D acoustics p, u_d (2 + 2); shallow water h, hu, hv (3 + 3); 3D
@@ -497,6 +522,9 @@ def main():
                     help="cell-updates/s from 256^2 to 16384^2 (one JSON line)")
     ap.add_argument("--accuracy", action="store_true",
                     help="errors of every workload against the oracle, with times (one JSON line)")
+    ap.add_argument("--only-extra", default=None,
+                    choices=["acoustics3d", "sw_bathymetry", "sw_unsplit", "ensembles"],
+                    help="run one extra measurement alone and print it")
     ap.add_argument("--fixed-segments", action="store_true",
                     help="with --paper-tables: 64-cell segments, no autotuning (for ncu)")
     args = ap.parse_args()
@@ -504,6 +532,14 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only_extra:
+        import torch
+        torch.cuda.set_device(0)
+        peak_gbs, _ = load_peaks()
+        fn = {"acoustics3d": extra_acoustics3d, "sw_bathymetry": extra_bathymetry,
+              "sw_unsplit": extra_unsplit, "ensembles": lambda a, p: extra_ensembles(a)}[args.only_extra]
+        print(json.dumps({args.only_extra: fn(args, peak_gbs)}), flush=True)
+        return 0
     if args.paper_tables or args.size_scaling or args.accuracy:
         import torch
         torch.cuda.set_device(0)
@@ -608,6 +644,7 @@ def main():
     if not args.no_extras and rank == 0:
         for key, fn in (("acoustics3d", lambda: extra_acoustics3d(args, peak_gbs)),
                         ("sw_bathymetry", lambda: extra_bathymetry(args, peak_gbs)),
+                        ("sw_unsplit", lambda: extra_unsplit(args, peak_gbs)),
                         ("ensembles", lambda: extra_ensembles(args))):
             try:
                 extras[key] = fn()

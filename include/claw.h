@@ -94,9 +94,16 @@ typedef struct { int ndim; int n[3]; double dx[3]; } claw_grid;
 /* Sweep order of a step.  GODUNOV: x(dt) y(dt) [z(dt)], Sec. 3 Eq.
  * LW-update as the paper runs it.  STRANG: x(dt/2) y(dt) x(dt/2) in 2D,
  * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D, the second-order splitting
- * of the same Clawpack base.  Either way a step's Courant number is
- * dt * max_d(m_d / dx_d), m_d the largest speed over the step's d sweeps. */
-typedef enum { CLAW_SPLIT_GODUNOV = 0, CLAW_SPLIT_STRANG = 1 } claw_splitting;
+ * of the same Clawpack base.  UNSPLIT (2D acoustics and shallow water, not
+ * CLAW_SHALLOW_WATER_BATHY; CLAW_EINVAL otherwise): no splitting -- every
+ * Riemann problem of the step is solved from Q^n and each cell is updated
+ * once from its x and y fluctuations and corrections, with transverse
+ * solvers carrying the fluctuations (modified by the corrections) across
+ * the neighbouring transverse interfaces (the unsplit form of Eq.
+ * LW-update in the same Clawpack base).  In every case a step's Courant
+ * number is dt * max_d(m_d / dx_d), m_d the largest speed along d in the
+ * step. */
+typedef enum { CLAW_SPLIT_GODUNOV = 0, CLAW_SPLIT_STRANG = 1, CLAW_SPLIT_UNSPLIT = 2 } claw_splitting;
 
 /* rho, K: constant acoustics coefficients (also the initial per-cell values
  * of CLAW_ACOUSTICS_VAR); g: gravity; cfl_desired: Courant number the next
@@ -247,8 +254,9 @@ claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system system,
 /* Take nsteps accepted steps like claw_run_steps inside one CUDA graph whose
  * kernels are bracketed by CUDA events, and report the average duration of
  * one launch of each kernel kind: kernel_ms[d] for the d-sweep (d < ndim;
- * with Strang splitting the sum over the step's d sweeps), kernel_ms[3]
- * for the step-control kernel; *total_ms for the whole graph.
+ * with Strang splitting the sum over the step's d sweeps; with
+ * CLAW_SPLIT_UNSPLIT kernel_ms[0] is the unsplit update and kernel_ms[1] is
+ * 0), kernel_ms[3] for the step-control kernel; *total_ms for the whole graph.
  * *launches receives the number of kernels launched.  Synchronises. */
 claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
                                double* total_ms, long* launches);
@@ -260,12 +268,16 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
 claw_status claw_probe_fma(int precision, double* flops_per_s, void* cuda_stream);
 
 /* Tuning knobs (the autotuner drives these): cells per line segment of one
- * thread in direction d (>= 4, rounded up to a multiple of 8).  Rebuilds the
- * tile lists. */
+ * thread in direction d (>= 4, rounded up to a multiple of 8).  With
+ * CLAW_SPLIT_UNSPLIT the direction-1 length is also the rows per strip tile
+ * of the unsplit update (a warp marches 28 columns down that many rows).
+ * Rebuilds the tile lists. */
 claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 
 /* Autotuner: for every direction, time trial_steps steps (CUDA events around
- * each sweep) twice with each candidate segment length and keep the fastest.  The
+ * each sweep) twice with each candidate segment length and keep the fastest
+ * (with CLAW_SPLIT_UNSPLIT: the rows per strip tile, timed on the unsplit
+ * kernel, from fixed lengths 16..256).  The
  * candidates are fixed lengths plus, for w = 1..4, the shortest length whose
  * tiles fit in w waves of the CTAs the GPU holds at once; a second pass
  * tries the lengths that split the longest line into equal whole chunks

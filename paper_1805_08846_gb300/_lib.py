@@ -133,7 +133,7 @@ def _stream_arg(stream):
     return C.c_void_p(int(stream))
 
 
-SPLITTINGS = {"godunov": 0, "strang": 1}
+SPLITTINGS = {"godunov": 0, "strang": 1, "unsplit": 2}
 
 
 def make_params(rho=1.0, K=1.0, g=9.81, cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, precision=64,

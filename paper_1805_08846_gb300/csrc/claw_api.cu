@@ -95,6 +95,11 @@ struct claw_solver {
     bool own_stream = false;
     std::map<int, cudaGraphExec_t> graphs;
     double Z = 0, c = 0;
+    // Unsplit update: one kernel per attempt over strip tiles (28 output
+    // columns x a segment of seg[1] rows).
+    bool unsplit = false;
+    std::vector<TileDesc> utiles;
+    TileDesc* d_utiles = nullptr;
 };
 
 namespace {
@@ -173,6 +178,33 @@ claw_status build_tiles(claw_solver* s) {
         CK(cudaMalloc(&s->d_order[d], sizeof(int) * std::max<size_t>(order.size(), 1)));
         CK(cudaMemcpy(s->d_order[d], order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
+    if (s->unsplit) {
+        // Strips of kStrip output columns x row segments of seg[1]; the
+        // strips of one row segment are adjacent in the list, so the warps
+        // of a CTA share their halo columns.
+        auto& T = s->utiles;
+        T.clear();
+        int strip = 0;
+        {
+            SweepLaunch L{};
+            L.system = s->system;
+            L.limiter = s->limiter;
+            L.precision = s->precision;
+            L.lines_out = &strip;
+            CK(launch_unsplit(L));
+        }
+        const int L = s->seg[1];
+        for (int i = 0; i < s->B; ++i) {
+            const InstDesc& I = s->inst[i];
+            for (int a = 0; a < I.n[1]; a += L)
+                for (int x0 = 0; x0 < I.n[0]; x0 += strip)
+                    T.push_back({i, x0, 0, a, std::min(a + L, I.n[1]), {0, 0, 0}});
+        }
+        if (s->d_utiles) cudaFree(s->d_utiles);
+        s->d_utiles = nullptr;
+        CK(cudaMalloc(&s->d_utiles, sizeof(TileDesc) * std::max<size_t>(T.size(), 1)));
+        CK(cudaMemcpy(s->d_utiles, T.data(), sizeof(TileDesc) * T.size(), cudaMemcpyHostToDevice));
+    }
     return CLAW_OK;
 }
 
@@ -246,8 +278,26 @@ long long tiles_for_segment(const claw_solver* s, int d, int L) {
     return t;
 }
 
+// The unsplit update of every instance (one kernel, four strip tiles per CTA).
+claw_status launch_unsplit_step(claw_solver* s) {
+    SweepLaunch L{};
+    L.args = sweep_args(s, 0, 0, 0, 0);
+    L.args.tiles = s->d_utiles;
+    L.args.order = nullptr;
+    L.args.persistent = 0;
+    L.args.ntiles = (int)s->utiles.size();
+    L.system = s->system;
+    L.limiter = s->limiter;
+    L.precision = s->precision;
+    L.grid = (unsigned)((s->utiles.size() + 3) / 4);
+    L.stream = s->stream;
+    CK(launch_unsplit(L));
+    return CLAW_OK;
+}
+
 // Sweep k of the step's sequence over every tile of its direction.
 claw_status launch_seq_sweep(claw_solver* s, int k) {
+    if (s->unsplit) return launch_unsplit_step(s);
     const int d = s->seq_dir[k];
     return launch_sweep_range(s, d, 0, (int)s->tiles[d].size(), false, k);
 }
@@ -456,8 +506,11 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     for (int k = 0; k < 2 * ndim; ++k)
         if (bc[k] < CLAW_BC_PERIODIC || bc[k] > CLAW_BC_WALL) return fail(CLAW_EINVAL, "unknown bc[%d] = %d", k, (int)bc[k]);
     if (params->precision != 32 && params->precision != 64) return fail(CLAW_EINVAL, "precision must be 32 or 64");
-    if (params->splitting != CLAW_SPLIT_GODUNOV && params->splitting != CLAW_SPLIT_STRANG)
+    if (params->splitting != CLAW_SPLIT_GODUNOV && params->splitting != CLAW_SPLIT_STRANG &&
+        params->splitting != CLAW_SPLIT_UNSPLIT)
         return fail(CLAW_EINVAL, "unknown splitting %d", params->splitting);
+    if (params->splitting == CLAW_SPLIT_UNSPLIT && (ndim != 2 || system == CLAW_SHALLOW_WATER_BATHY))
+        return fail(CLAW_EINVAL, "the unsplit update covers 2D acoustics and shallow water without bathymetry");
     if (!(params->cfl_desired > 0.0) || !(params->cfl_max > 0.0)) return fail(CLAW_EINVAL, "cfl_desired and cfl_max must be > 0");
     if (!(params->dt_max > 0.0)) return fail(CLAW_EINVAL, "dt_max must be > 0");
     if (!is_sw(system) && (!(params->rho > 0.0) || !(params->K > 0.0)))
@@ -571,7 +624,18 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     // writes the next one; versions after Q^n alternate between slots 1 and
     // 2, so Q^n stays intact until the step is accepted.
     s->nseq = 0;
-    if (params->splitting == CLAW_SPLIT_STRANG) {
+    s->unsplit = params->splitting == CLAW_SPLIT_UNSPLIT;
+    if (s->unsplit) {
+        // one update per step from Q^n: every field read from the kept
+        // slot and written to the next one
+        s->nseq = 1;
+        s->seq_dir[0] = 0;
+        s->seq_frac[0] = 1.0;
+        memset(&s->seq_slots[0], 0, sizeof(SlotMap));
+        for (int f = 0; f < m; ++f) s->seq_slots[0].out_off[f] = 1;
+        s->fin.m = m;
+        for (int f = 0; f < 4; ++f) s->fin.off[f] = f < m ? 1 : 0;
+    } else if (params->splitting == CLAW_SPLIT_STRANG) {
         for (int d = 0; d < ndim - 1; ++d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 0.5; }
         s->seq_dir[s->nseq] = ndim - 1; s->seq_frac[s->nseq++] = 1.0;
         for (int d = ndim - 2; d >= 0; --d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 0.5; }
@@ -579,7 +643,7 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
         for (int d = 0; d < ndim; ++d) { s->seq_dir[s->nseq] = d; s->seq_frac[s->nseq++] = 1.0; }
     }
     int ver[4] = {0, 0, 0, 0};
-    for (int k = 0; k < s->nseq; ++k) {
+    for (int k = 0; k < s->nseq && !s->unsplit; ++k) {
         memset(&s->seq_slots[k], 0, sizeof(SlotMap));
         for (int f : touched_fields(system, s->seq_dir[k])) {
             s->seq_slots[k].in_off[f] = (signed char)slot_of_version(ver[f]);
@@ -587,8 +651,10 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
             ver[f] += 1;
         }
     }
-    s->fin.m = m;
-    for (int f = 0; f < 4; ++f) s->fin.off[f] = slot_of_version(ver[f]);
+    if (!s->unsplit) {
+        s->fin.m = m;
+        for (int f = 0; f < 4; ++f) s->fin.off[f] = slot_of_version(ver[f]);
+    }
 
     CKS(build_tiles(s));
     // Initial state: zero (h = 1 for shallow water); material from params.
@@ -678,6 +744,14 @@ claw_status set_bathymetry_impl(claw_solver* s, int i, const double* B, int on_d
 
 void claw::set_last_error(const char* msg) { g_err = msg; }
 
+cudaError_t claw::launch_unsplit(const SweepLaunch& L) {
+    if (L.system == kSysShallowWater)
+        return L.precision == 64 ? launch_unsplit_shallow_water_f64(L) : launch_unsplit_shallow_water_f32(L);
+    if (L.system == kSysAcoustics || L.system == kSysAcousticsVar)
+        return L.precision == 64 ? launch_unsplit_acoustics_f64(L) : launch_unsplit_acoustics_f32(L);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t claw::launch_sweep(const SweepLaunch& L) {
     switch (L.system) {
         case kSysAcoustics:
@@ -735,6 +809,7 @@ void claw_destroy(claw_solver* s) {
         if (s->d_tiles[d]) cudaFree(s->d_tiles[d]);
         if (s->d_order[d]) cudaFree(s->d_order[d]);
     }
+    if (s->d_utiles) cudaFree(s->d_utiles);
     if (s->d_counters) cudaFree(s->d_counters);
     if (s->pool) cudaFree(s->pool);
     if (s->aux) cudaFree(s->aux);
@@ -884,7 +959,30 @@ claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
     static const int cand_t[] = {8, 16, 24, 32, 48, 64, 96, 128, 256};
     int best[3] = {s->seg[0], s->seg[1], s->seg[2]};
     claw_status st = CLAW_OK;
-    for (int d = 0; d < s->ndim && st == CLAW_OK; ++d) {
+    if (s->unsplit) {
+        // One kernel per step: the rows per strip tile (seg[1]) are the
+        // only knob; its time is kernel_ms[0].
+        static const int cand_u[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
+        int maxN = 0;
+        for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[1]);
+        double best_ms = 1e30;
+        for (int k = 0; k < 9 && st == CLAW_OK; ++k) {
+            if (cand_u[k] > 2 * maxN && k > 0) break;
+            st = claw_set_segment(s, 1, cand_u[k]);
+            for (int rep = 0; rep < 2 && st == CLAW_OK; ++rep) {
+                double ms[4], tot;
+                long nl;
+                st = claw_profile_steps(s, trial_steps, ms, &tot, &nl);
+                if (st == CLAW_OK && ms[0] < best_ms) {
+                    best_ms = ms[0];
+                    best[1] = s->seg[1];
+                }
+                if (st == CLAW_OK) st = restore();
+            }
+        }
+        if (st == CLAW_OK) st = claw_set_segment(s, 1, best[1]);
+    }
+    for (int d = 0; d < s->ndim && st == CLAW_OK && !s->unsplit; ++d) {
         int maxN = 0;
         for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[d]);
         // Fixed lengths, plus for w = 1..4 the shortest segment whose tiles

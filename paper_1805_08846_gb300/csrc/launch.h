@@ -35,6 +35,16 @@ cudaError_t launch_sweep_shallow_water_f64(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_bathy_f32(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_bathy_f64(const SweepLaunch& L);
 
+// Unsplit update with transverse waves (2D acoustics and shallow water):
+// one launch per step attempt over the strip tiles in args.tiles (TileDesc:
+// line0 = first output column of a 28-column strip, [a, b) = rows), grid =
+// CTAs of four one-warp tiles.  lines_out reports the output columns of a strip.
+cudaError_t launch_unsplit(const SweepLaunch& L);
+cudaError_t launch_unsplit_acoustics_f32(const SweepLaunch& L);
+cudaError_t launch_unsplit_acoustics_f64(const SweepLaunch& L);
+cudaError_t launch_unsplit_shallow_water_f32(const SweepLaunch& L);
+cudaError_t launch_unsplit_shallow_water_f64(const SweepLaunch& L);
+
 struct FinalSlots {
     int off[4];      // slot offset of each field's result after a full step
     int m;

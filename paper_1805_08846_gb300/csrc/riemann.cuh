@@ -236,7 +236,17 @@ struct ShallowWater {
 
     __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
                                                  Waves<Real, NQ, NW>& w) {
-        Real uh, vh, ch, i2c, ni2c;
+        Real uh, vh, ch, i2c;
+        solve(l, r, P, w, uh, vh, ch, i2c);
+    }
+
+    // The same, also returning the interface's Roe averages u_hat, v_hat,
+    // c_hat and 1 / (2 c_hat) (the unsplit update's transverse solvers
+    // reuse them).
+    __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
+                                                 Waves<Real, NQ, NW>& w, Real& uh, Real& vh, Real& ch,
+                                                 Real& i2c) {
+        Real ni2c;
         roe(l, r, P, uh, vh, ch, i2c, ni2c);
         // strengths with nd0 = -(h_r - h_l) so that no operand needs negating:
         //   a1 = (s3 d0 - d1) / 2c,  a2 = d2 - vh d0,  a3 = (d1 - s1 d0) / 2c
