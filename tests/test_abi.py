@@ -58,6 +58,9 @@ def _create(**over):
     (dict(params=L.make_params(cfl_desired=0.0)), "cfl_desired"),
     (dict(params=L.make_params(g=-1.0)), "g must be"),
     (dict(params=L.make_params(splitting=7)), "unknown splitting"),
+    (dict(n=(8, 8, 8), dx=(0.1, 0.1, 0.1), system="acoustics", m=4, mwaves=2,
+          params=L.make_params(splitting="unsplit")), "unsplit update covers"),
+    (dict(system="shallow_water_bathy", params=L.make_params(splitting="unsplit")), "unsplit update covers"),
     (dict(system="acoustics", m=3, mwaves=2, params=L.make_params(rho=0.0)), "rho and K"),
     (dict(system=7), "unknown system"),
     (dict(limiter=9), "unknown limiter"),
