@@ -393,7 +393,9 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
     }
 
     const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
-#pragma unroll 1
+    // unrolled by two rows (measured at 4096^2: 0.526 -> 0.503 ms; three rows
+    // need more registers than three CTAs per SM allow and run at 0.63 ms)
+#pragma unroll 2
     for (int R = a - 2; R <= b + 1; ++R) {
         Full cur;
         U::set(cur, n0.q, n0.m, P);
