@@ -38,16 +38,21 @@ METRIC = "cell-updates/s"
 SW_FLOP_PER_CELL_SWEEP = 313.0 / 2.0
 
 
-def kernel_source_digest():
-    """Digest of the CUDA sources: a traffic record taken with ncu is valid
-    only for the kernels it was taken on."""
+# Files the FP32 shallow-water sweep kernels are compiled from (the unit
+# that instantiates them and every header it includes) and the build flags.
+SWEEP_SOURCES = ("sweep_shallow_water_f32.cu", "sweep_dispatch.cuh", "launch.h", "sweep.cuh",
+                 "claw_types.cuh", "riemann.cuh", "pair.cuh", "tma.cuh", "../build.py")
+
+
+def kernel_source_digest(files=SWEEP_SOURCES):
+    """Digest of the sources the profiled kernels are built from: a traffic
+    record taken with ncu is valid only for the kernels it was taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1805_08846_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -577,20 +582,38 @@ def main():
                 s.set_segment(d, L_)
         else:
             segs[precision] = s.autotune(4)           # tile shapes (state restored)
-        s.run_steps(args.warmup)                      # warm-up: graphs, caches, clocks
+        # Untimed set-up: the CUDA graph of the timed call length is captured
+        # once (like compilation), then the state and clock start over.
+        s.run_steps(args.steps)
+        s.set_q(prob.q0)
+        s.set_time(0.0, 0.0, 0)
+        s.run_steps(args.warmup)                      # warm-up steps: caches, clocks
+        stream = torch.cuda.current_stream()
+        rej0 = s.rejections()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         barrier(world)
         torch.cuda.synchronize()
-        ms, total_ms, launches = s.profile_steps(args.steps)
+        e0.record(stream)
+        s.run_steps(args.steps)                       # the timed call: one graph replay
+        e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-        total_ms = max_over_ranks(total_ms, world)
-        q_after = None
+        total_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        rej = s.rejections() - rej0
+        # Per-kernel durations: a separate graph of the same steps with CUDA
+        # events around every kernel (the events slow the graph a little, so
+        # this pass gives the kernel breakdown, not the step rate).
+        ms, prof_ms, _ = s.profile_steps(args.steps)
         s.close()
-        return ms, total_ms, launches
+        # kernels of the timed call: the arming kernel, then per attempt
+        # (kept steps and redone ones) two sweeps and the step control
+        launches = 1 + (args.steps + rej) * 3
+        return ms, total_ms, launches, prof_ms, rej
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms32, tot32, launches = timed(32)
+    ms32, tot32, launches, prof32, rej32 = timed(32)
     clk = clocks.stop()
     value = world * ncell * args.steps / (tot32 * 1e-3)
 
@@ -608,6 +631,11 @@ def main():
     s = Solver.from_problem(prob, precision=32, stream="torch")
     for d, L_ in enumerate(segs[32][:2]):
         s.set_segment(d, L_)
+    # untimed pass of the same calls (captures the graph of the timed call length)
+    s.set_q(q_host)
+    s.run_steps(args.steps)
+    s.get_q(out_host)
+    s.set_q(q_host)
     s.run_steps(args.warmup)
     torch.cuda.synchronize()
     barrier(world)
@@ -623,7 +651,7 @@ def main():
 
     fp64 = None
     if not args.no_fp64:
-        ms64, tot64, _ = timed(64)
+        ms64, tot64, _, _, _ = timed(64)
         fma64 = L.claw_probe_fma(64)
         dom64 = 0 if ms64[0] >= ms64[1] else 1
         ach64 = SW_FLOP_PER_CELL_SWEEP * ncell / (ms64[dom64] * 1e-3)
@@ -663,6 +691,9 @@ def main():
                    "global_batch": world, "seq_len": ncell,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (201 MB per FP32 state version vs 129 MB L2)",
+                   "timing": "CUDA events around one claw_run_steps call (one graph replay of all "
+                             "steps; its graph captured in an untimed run first); per-kernel times "
+                             "from a separate claw_profile_steps graph with events around each kernel",
                    "segments": {"f32": segs.get(32, [])[:2], "f64": segs.get(64, [])[:2]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                      "frac": achieved / peak_gbs, "traffic": traffic,
@@ -673,6 +704,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": state_bytes / args.steps},
         "gpu_launches": launches,
+        "rejected_attempts": rej32,
+        "kernel_breakdown_ms_per_step": prof32 / args.steps,
         "clocks": clk,
         "fp64_plain": fp64,
     }

@@ -270,7 +270,10 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
     Control* ctl = A.ctl + td.inst;
     if (*(volatile int*)&ctl->active == 0) return;
 
+    // geometry in registers: the stores through qout below could otherwise
+    // make the compiler reload these from the descriptor after every store
     const int nx = I.n[0], ny = I.n[1];
+    const long long pitch = I.pitch, fstride = I.fstride;
     const int a = td.a, b = td.b;
     int col = td.line0 - 2 + lane;
     const bool out_lane = lane >= 2 && lane < 2 + kStrip && col < nx;
@@ -308,13 +311,13 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
     auto load = [&](int R, Raw& r) {
         bool flip_y;
         const int sr = map_cell(R, ny, bc_ylo, bc_yhi, flip_y);
-        const long long o = (long long)sr * I.pitch + src_col;
+        const long long o = (long long)sr * pitch + src_col;
 #pragma unroll
         for (int f = 0; f < 3; ++f) r.q[f] = __ldg(qin[f] + o);
         if (flip_x) r.q[1] = -r.q[1];
         if (flip_y) r.q[2] = -r.q[2];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) r.m[k] = __ldg(aux + k * I.fstride + o);
+        for (int k = 0; k < NA; ++k) r.m[k] = __ldg(aux + k * fstride + o);
     };
 
     const double dt = ctl->dt_attempt * A.dt_scale;
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
                 qn[f] = vfma(-nu_y, Gn[c] - G2[c], qn[f]);
             }
             if (out_lane) {
-                const long long o = (long long)(R - 2) * I.pitch + col;
+                const long long o = (long long)(R - 2) * pitch + col;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) qout[f][o] = qn[f];
                 if constexpr (Sys::kMinH) {
