@@ -481,6 +481,58 @@ def extra_ensembles(args):
     return res
 
 
+def slab_bench(args):
+    """One 2D grid split along y across the ranks (strong scaling): each rank
+    a Solver over its slab with a halo of 2K rows, K steps per halo refresh
+    (all-gather over NCCL), one step size agreed per period (all-reduce).
+    value = cells of the whole grid x steps / the slowest rank's time."""
+    import torch
+    from paper_1805_08846_gb300 import Solver, inputs
+    from paper_1805_08846_gb300 import slab as S
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prob = inputs.sw_radial_dam_break(args.n)
+    k = args.period
+    layout = S.SlabLayout(prob.n[1], world, 2 * k, False)
+    lp = S.local_problem(prob, layout, rank)
+    solver = Solver.from_problem(lp, precision=32)
+    seg = solver.autotune(2)
+    steppers = {rank: S.solver_stepper(solver)}
+    comm = S.DistComm() if world > 1 else S.LocalComm()
+    S.run_steps(steppers, layout, comm, args.warmup, k)
+    S.run_steps(steppers, layout, comm, args.steps, k)   # captures the graphs of the period lengths
+    solver.set_q(lp.q0)
+    S.run_steps(steppers, layout, comm, args.warmup, k)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = S.run_steps(steppers, layout, comm, args.steps, k)
+    torch.cuda.synchronize()
+    barrier(world)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    solver.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": prob.ncells * args.steps / el, "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"2D shallow water radial dam break {args.n}x{args.n} split into "
+                                   f"{world} slabs along y, halo {2 * k} rows, {k} steps per refresh",
+                       "parallelism": f"slab{world}", "segments": seg[:2],
+                       "timing": "wall clock of the decomposed run: per period a halo refresh, a "
+                                 "speed pass, a state snapshot and one graph of fixed steps"},
+            "periods": info.periods, "redone": info.redone, "cfl_max_seen": info.cfl_max_seen}),
+            flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def reference_arm(args):
     """The oracle as the reference arm: each step is the full step of the
     workload on a bounded subset of its lines (the x sweep on the first L rows
@@ -551,6 +603,10 @@ def main():
                     help="cell-updates/s from 256^2 to 16384^2 (one JSON line)")
     ap.add_argument("--accuracy", action="store_true",
                     help="errors of every workload against the oracle, with times (one JSON line)")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="replicas: every rank its own grid (weak scaling, the default); "
+                         "slab: one grid split along y across the ranks (strong scaling)")
+    ap.add_argument("--period", type=int, default=8, help="with --decomp slab: steps per halo refresh")
     ap.add_argument("--only-extra", default=None,
                     choices=["acoustics3d", "sw_bathymetry", "sw_unsplit", "ensembles"],
                     help="run one extra measurement alone and print it")
@@ -561,6 +617,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.decomp == "slab":
+        return slab_bench(args)
     if args.only_extra:
         import torch
         torch.cuda.set_device(0)

@@ -190,6 +190,27 @@ claw_status claw_conservation_sums(claw_solver* s, double* sums);
 /* Rejected attempts so far.  Synchronises. */
 claw_status claw_get_rejections(claw_solver* s, long* nrej);
 
+/* nsteps steps of exactly dt > 0, all kept (no CFL decision), replayed as
+ * CUDA graphs like claw_run_steps; *cfl_peak (may be NULL) receives the
+ * largest Courant number dt * max_d(m_d / dx_d) among them, so a caller that
+ * decides the step size itself -- e.g. over several solvers holding pieces
+ * of one grid (Sec. 8: independent subproblems advanced for several steps)
+ * -- can check the CFL condition (Eq. CFL-condition) afterwards.  For an
+ * ensemble, the largest over the instances.  Synchronises. */
+claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* cfl_peak);
+
+/* Rows [y0, y0 + nrows) of every field of a single 2D grid, FP64,
+ * structure of arrays (m, nrows, nx), x fastest: copied out of (get) or
+ * into (set) the current state.  The pieces of a grid split along y
+ * exchange their boundary rows this way.  on_device as for claw_set_q.
+ * claw_set_rows leaves the next step size as it is (claw_max_speed gives the
+ * speeds of the new state); it is asynchronous for a device buffer, which
+ * must stay valid until the solver's stream reaches the copy.  claw_get_rows
+ * synchronises.  CLAW_EINVAL for an ensemble or a 3D grid, CLAW_EBOUNDS for
+ * rows outside [0, ny). */
+claw_status claw_get_rows(claw_solver* s, int y0, int nrows, double* out, int on_device);
+claw_status claw_set_rows(claw_solver* s, int y0, int nrows, const double* rows, int on_device);
+
 /* Thread-local text of the last failure ("" if none). */
 const char* claw_last_error(void);
 

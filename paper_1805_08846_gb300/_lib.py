@@ -58,6 +58,9 @@ _SIGS = {
     "claw_set_time": [_vp, C.c_double, C.c_double, C.c_long],
     "claw_conservation_sums": [_vp, _dp],
     "claw_get_rejections": [_vp, C.POINTER(C.c_long)],
+    "claw_run_fixed_steps": [_vp, C.c_int, C.c_double, _dp],
+    "claw_get_rows": [_vp, C.c_int, C.c_int, _vp, C.c_int],
+    "claw_set_rows": [_vp, C.c_int, C.c_int, _vp, C.c_int],
     "claw_last_error": [],
     "claw_ensemble_create": [C.c_int, C.POINTER(claw_grid), C.c_int, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(claw_params), _vp, C.POINTER(_vp)],
@@ -194,6 +197,26 @@ def claw_destroy(h):
 def claw_set_q(h, q):
     p, dev, keep = _array_arg(q)
     _check(lib().claw_set_q(h, p, dev), "claw_set_q")
+
+
+def claw_run_fixed_steps(h, nsteps, dt):
+    cfl = C.c_double(0.0)
+    _check(lib().claw_run_fixed_steps(h, int(nsteps), float(dt), C.byref(cfl)), "claw_run_fixed_steps")
+    return cfl.value
+
+
+def claw_get_rows(h, y0, out):
+    """Rows y0 .. y0 + out.shape[1] - 1 into `out` (m, nrows, nx)."""
+    p, dev, keep = _array_arg(out)
+    if not dev and keep is not out:
+        raise ValueError("host output must be a contiguous float64 numpy array")
+    _check(lib().claw_get_rows(h, int(y0), int(out.shape[1]), p, dev), "claw_get_rows")
+    return out
+
+
+def claw_set_rows(h, y0, rows):
+    p, dev, keep = _array_arg(rows)
+    _check(lib().claw_set_rows(h, int(y0), int(rows.shape[1]), p, dev), "claw_set_rows")
 
 
 def claw_get_q(h, out):

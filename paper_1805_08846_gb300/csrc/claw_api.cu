@@ -723,6 +723,37 @@ claw_status set_aux_impl(claw_solver* s, int i, const double* rho, const double*
     return CLAW_OK;
 }
 
+// Rows [y0, y0 + nrows) of every field of a 2D grid, FP64 (m, nrows, nx),
+// into (in = true) or out of the kept state: the conversion kernels run on a
+// descriptor whose origin is row y0 and whose height is nrows.
+claw_status rows_impl(claw_solver* s, int y0, int nrows, double* buf, int on_device, bool in) {
+    CKS(check_solver(s));
+    if (!buf) return fail(CLAW_EINVAL, "rows buffer is NULL");
+    if (s->ndim != 2 || s->B != 1) return fail(CLAW_EINVAL, "row access is for a single 2D grid");
+    const InstDesc& I = s->inst[0];
+    if (y0 < 0 || nrows < 1 || y0 > I.n[1] - nrows)
+        return fail(CLAW_EBOUNDS, "rows [%d, %d) outside [0, %d)", y0, y0 + nrows, I.n[1]);
+    InstDesc W = I;
+    W.offset += (long long)y0 * I.pitch;
+    W.n[1] = nrows;
+    const size_t n = (size_t)I.n[0] * nrows * s->m;
+    if (in) {
+        const double* src = buf;
+        if (!on_device) {
+            CK(cudaMemcpyAsync(s->stage, buf, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+            src = s->stage;
+        }
+        CK(launch_convert_in(s->precision, s->pool, W, s->d_ctl, src, s->m, s->stream));
+        if (!on_device) CK(cudaStreamSynchronize(s->stream));   // the host buffer may go away
+        return CLAW_OK;
+    }
+    double* dst = on_device ? buf : s->stage;
+    CK(launch_convert_out(s->precision, s->pool, W, s->d_ctl, dst, s->m, s->stream));
+    if (!on_device) CK(cudaMemcpyAsync(buf, s->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CKS(read_ctl(s));
+    return latched_status(s, 0, 1);
+}
+
 claw_status set_bathymetry_impl(claw_solver* s, int i, const double* B, int on_device) {
     CKS(check_solver(s, i));
     if (s->system != CLAW_SHALLOW_WATER_BATHY)
@@ -844,12 +875,31 @@ claw_status claw_ensemble_set_bathymetry(claw_solver* s, int i, const double* B,
     return set_bathymetry_impl(s, i, B, on_device);
 }
 int claw_ensemble_size(const claw_solver* s) { return s ? s->B : 0; }
+claw_status claw_get_rows(claw_solver* s, int y0, int nrows, double* out, int on_device) {
+    return rows_impl(s, y0, nrows, out, on_device, false);
+}
+claw_status claw_set_rows(claw_solver* s, int y0, int nrows, const double* rows, int on_device) {
+    return rows_impl(s, y0, nrows, const_cast<double*>(rows), on_device, true);
+}
 
 claw_status claw_step(claw_solver* s, double dt, double* cfl_out) {
     CKS(check_solver(s));
     CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, 1, 0.0, dt > 0.0 ? dt : 0.0, 0.0, s->d_counters, s->stream));
     CKS(run_armed(s, kModeSteps, 1));
     if (cfl_out) *cfl_out = s->h_ctl[0].cfl_last;
+    return CLAW_OK;
+}
+
+claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* cfl_peak) {
+    CKS(check_solver(s));
+    if (nsteps < 0) return fail(CLAW_EINVAL, "nsteps < 0");
+    if (!(dt > 0.0)) return fail(CLAW_EINVAL, "dt must be > 0");
+    if (cfl_peak) *cfl_peak = 0.0;
+    if (nsteps == 0) return CLAW_OK;
+    CK(launch_arm(s->d_ctl, 0, s->B, kModeSteps, nsteps, 0.0, dt, 0.0, s->d_counters, s->stream));
+    CKS(run_armed(s, kModeSteps, nsteps));
+    if (cfl_peak)
+        for (int i = 0; i < s->B; ++i) *cfl_peak = std::max(*cfl_peak, s->h_ctl[i].cfl_peak);
     return CLAW_OK;
 }
 

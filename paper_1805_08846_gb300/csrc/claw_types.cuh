@@ -50,6 +50,7 @@ struct Control {
     double dt_attempt;     // step size the sweeps of the current attempt use
     double fixed_dt;       // > 0: fixed step, no CFL control
     double cfl_last;       // Courant number of the last attempt
+    double cfl_peak;       // largest Courant number of the steps kept since arming
     double cfl_desired;
     double cfl_max;
     double dt_max;

@@ -62,6 +62,7 @@ __global__ void arm_kernel(Control* ctl, int lo, int hi, int mode, long long nst
     c.streak = 0;
     c.smax[0] = c.smax[1] = c.smax[2] = 0ull;
     c.bad = 0u;
+    c.cfl_peak = 0.0;
     prepare_attempt(c);
 }
 
@@ -107,6 +108,7 @@ __global__ void finish_kernel(Control* ctl, const InstDesc* inst, int lo, int hi
         }
     } else {
         c.streak = 0;
+        if (cfl > c.cfl_peak) c.cfl_peak = cfl;
         for (int f = 0; f < fs.m; ++f) c.cur[f] = (c.cur[f] + fs.off[f]) % 3;
         c.t = c.last ? c.t_final : c.t + c.dt_attempt;
         c.nacc += 1;

@@ -7,7 +7,7 @@ fed from it without sharing any numerical code.
 
 Every workload restates one of the five benchmark problems (2D acoustics
 pulse, 2D radial dam break, 3D two-layer acoustics, 2D shallow-water
-ensemble, 3D acoustics ensemble) with the readings documented in the design doc:
+ensemble, 3D acoustics ensemble) with these readings where the paper is silent:
 cell centres at ``lower + (i + 1/2) dx``, point-sampled initial data,
 seed 1805 through ``numpy.random.Generator(PCG64(seed))``.
 
@@ -52,6 +52,9 @@ class Problem:
     name: str = ""
     splitting: str = "godunov"    # one of SPLITTINGS
     B_cell: Optional[np.ndarray] = None     # (ny, nx) bottom elevation for shallow_water_bathy
+    # cell widths given exactly (a piece of a larger grid keeps its parent's
+    # widths; recomputing them from the piece's bounds can differ in the last bit)
+    cell_width: Optional[tuple] = None
 
     @property
     def m(self) -> int:
@@ -63,6 +66,8 @@ class Problem:
 
     @property
     def dx(self) -> tuple:
+        if self.cell_width is not None:
+            return tuple(self.cell_width)
         return tuple((self.upper[d] - self.lower[d]) / self.n[d] for d in range(self.ndim))
 
     @property

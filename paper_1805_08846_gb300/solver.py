@@ -87,6 +87,16 @@ class Solver:
     def max_speed(self):
         return L.claw_max_speed(self.h)
 
+    def run_fixed_steps(self, nsteps, dt):
+        """nsteps kept steps of exactly dt; returns the largest Courant number."""
+        return L.claw_run_fixed_steps(self.h, nsteps, dt)
+
+    def get_rows(self, y0, out):
+        return L.claw_get_rows(self.h, y0, out)
+
+    def set_rows(self, y0, rows):
+        L.claw_set_rows(self.h, y0, rows)
+
     def time(self):
         return L.claw_get_time(self.h)
 
