@@ -83,8 +83,14 @@ _lib = None
 _lock = threading.Lock()
 
 
+def debug_build() -> bool:
+    """CLAW_DEBUG=1 in the environment selects the checked library (bounds
+    checks of the kernels' global accesses, reported as CLAW_EBOUNDS)."""
+    return os.environ.get("CLAW_DEBUG", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_build() else _build.LIB
 
 
 def lib():
@@ -92,7 +98,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=debug_build())
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library missing: {path}")
             L = C.CDLL(path)

@@ -2,8 +2,10 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel
 (``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``) and linked
-into ``paper_1805_08846_gb300/_build/libclaw.so``.  Nothing is installed
-outside this directory.
+into ``paper_1805_08846_gb300/_build/libclaw.so``.  ``build(debug=True)``
+makes the checked variant (``-DCLAW_DEBUG``: bounds checks of every direct
+global access and bulk-copy coordinate in the kernels) in
+``_build_debug/libclaw.so``.  Nothing is installed outside this directory.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libclaw.so")
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libclaw.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -37,10 +41,10 @@ def headers():
     return hs + [os.path.join(INCLUDE, "claw.h"), os.path.abspath(__file__)]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in sources()] + headers()
     return any(os.path.getmtime(p) > t for p in deps)
 
@@ -50,8 +54,8 @@ def flags():
             "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
-def _compile(src: str, verbose: bool, extra) -> str:
-    obj = os.path.join(OUT, src[:-3] + ".o")
+def _compile(src: str, verbose: bool, extra, out: str = OUT) -> str:
+    obj = os.path.join(out, src[:-3] + ".o")
     cmd = [nvcc()] + flags() + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
@@ -63,20 +67,23 @@ def _compile(src: str, verbose: bool, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    if debug:
+        extra = list(extra) + ["-DCLAW_DEBUG"]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, extra), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, extra, out), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), ARCH, "-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -70,6 +70,39 @@ struct Control {
     int pad;
 };
 
+// Debug builds (-DCLAW_DEBUG, the library the CLAW_DEBUG=1 environment loads)
+// check the kernels' direct global accesses, in place of a memory checker:
+// an element offset o inside a field or material plane of instance I must
+// name an interior cell (0 <= o < fstride and o mod pitch < nx), and a bulk
+// copy's coordinates must lie in their ranges.  A failed check latches
+// kStatBounds (CLAW_EBOUNDS at the next synchronising call) and the caller
+// skips the access.  In release builds both checks are the constant true.
+#ifdef CLAW_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+
+__device__ __forceinline__ bool cell_ok(long long o, const InstDesc& I, Control* ctl) {
+    if constexpr (kDebugChecks) {
+        if (o < 0 || o >= I.fstride || o % I.pitch >= I.n[0]) {
+            atomicOr(&ctl->status, kStatBounds);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool index_ok(long long i, long long n, Control* ctl) {
+    if constexpr (kDebugChecks) {
+        if (i < 0 || i >= n) {
+            atomicOr(&ctl->status, kStatBounds);
+            return false;
+        }
+    }
+    return true;
+}
+
 // One tile of a sweep: kLines consecutive lines of one instance and the
 // segment [a, b) of each line along the sweep direction.  For the x sweep the
 // lines are rows r = line0 + t of the flattened (z, y) index; for the y (z)

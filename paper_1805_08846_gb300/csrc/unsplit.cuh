@@ -312,12 +312,13 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
         bool flip_y;
         const int sr = map_cell(R, ny, bc_ylo, bc_yhi, flip_y);
         const long long o = (long long)sr * pitch + src_col;
+        const bool ok = cell_ok(o, I, ctl);
 #pragma unroll
-        for (int f = 0; f < 3; ++f) r.q[f] = __ldg(qin[f] + o);
+        for (int f = 0; f < 3; ++f) r.q[f] = ok ? __ldg(qin[f] + o) : Real(1);
         if (flip_x) r.q[1] = -r.q[1];
         if (flip_y) r.q[2] = -r.q[2];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) r.m[k] = __ldg(aux + k * fstride + o);
+        for (int k = 0; k < NA; ++k) r.m[k] = ok ? __ldg(aux + k * fstride + o) : Real(1);
     };
 
     const double dt = ctl->dt_attempt * A.dt_scale;
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(32 * kUnsplitWarps)
                 qn[f] = vfma(-nu_y, ayf[c], qn[f]);
                 qn[f] = vfma(-nu_y, Gn[c] - G2[c], qn[f]);
             }
-            if (out_lane) {
+            if (out_lane && cell_ok((long long)(R - 2) * pitch + col, I, ctl)) {
                 const long long o = (long long)(R - 2) * pitch + col;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) qout[f][o] = qn[f];
