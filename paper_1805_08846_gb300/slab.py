@@ -41,7 +41,7 @@ on one device.
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Dict, List, Sequence
+from typing import Dict, List
 
 
 @dataclass(frozen=True)
