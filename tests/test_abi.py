@@ -87,4 +87,7 @@ def test_null_solver_is_rejected():
     lib = L.lib()
     assert lib.claw_run_steps(None, 1) == L.CLAW_EINVAL
     assert lib.claw_step(None, 0.0, None) == L.CLAW_EINVAL
+    assert lib.claw_run_fixed_steps(None, 2, 0.1, None) == L.CLAW_EINVAL
+    assert lib.claw_get_rows(None, 0, 1, None, 0) == L.CLAW_EINVAL
+    assert lib.claw_set_rows(None, 0, 1, None, 0) == L.CLAW_EINVAL
     lib.claw_destroy(None)
