@@ -243,8 +243,8 @@ def gather_grid(steppers: Dict[int, "object"], layout: SlabLayout, comm):
 
 class solver_stepper:
     """A rank's compute on its GPU: a `Solver` over the local grid.  Steps
-    are fixed (claw_run_fixed_steps; the CFL decision is the driver's, made
-    on the speeds of all ranks), rows cross through claw_get_rows /
+    are fixed (claw_run_fixed_steps; run_steps takes the CFL decision on the
+    speeds of all ranks), rows cross through claw_get_rows /
     claw_set_rows as float64 torch tensors on `device` ("cpu" for gloo:
     host tensors, copied), and the period's start is kept as a device copy
     of the state for a redo."""
