@@ -65,8 +65,8 @@ def single_grid(prob, dts):
     return q
 
 
-def problem(split, ybc, shape=(30, 37), seed=3):
-    p = inputs.random_problem("shallow_water", shape, "mc", ("extrap", "wall", ybc, ybc),
+def problem(split, ybc, shape=(30, 37), seed=3, system="shallow_water"):
+    p = inputs.random_problem(system, shape, "mc", ("extrap", "wall", ybc, ybc),
                               seed=seed, discontinuous=True)
     q0 = p.q0.copy()
     q0[0, shape[1] // 3: shape[1] // 2, :] += 0.4           # a jump across the cuts' rows
@@ -165,6 +165,16 @@ def test_three_slabs_in_one_process_equal_the_single_grid(split, ybc):
     prob = problem(split, ybc)
     q, info = run_local(prob, 3, k=2, nsteps=5)
     assert info.periods == 3 and len(info.dts) == 5
+    np.testing.assert_array_equal(q, single_grid(prob, info.dts))
+
+
+@pytest.mark.parametrize("system,split", [("acoustics_var", "godunov"), ("acoustics_var", "unsplit"),
+                                          ("shallow_water_bathy", "strang")])
+def test_slabs_carry_their_rows_of_the_material_arrays(system, split):
+    """Per-cell rho, K and the bottom elevation are cut into the slabs with
+    their halos: the decomposed run still equals the single grid."""
+    prob = problem(split, "periodic", system=system)
+    q, info = run_local(prob, 3, k=2, nsteps=4)
     np.testing.assert_array_equal(q, single_grid(prob, info.dts))
 
 
