@@ -209,6 +209,17 @@ claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* 
  * synchronises.  CLAW_EINVAL for an ensemble or a 3D grid, CLAW_EBOUNDS for
  * rows outside [0, ny). */
 claw_status claw_get_rows(claw_solver* s, int y0, int nrows, double* out, int on_device);
+
+/* Keep a copy of the current state (every field's kept version, in the
+ * state's precision, in device memory the solver allocates on the first call:
+ * one state version) and of the clock and step control; claw_rollback
+ * returns to it, bitwise -- state, t, next dt, step counts.  A caller that
+ * takes a period of fixed steps and may have to redo it (the CFL condition
+ * checked afterwards, Eq. CFL-condition) keeps the period's start this way
+ * without a round trip through FP64.  claw_rollback without a checkpoint:
+ * CLAW_EINVAL.  Both synchronise. */
+claw_status claw_checkpoint(claw_solver* s);
+claw_status claw_rollback(claw_solver* s);
 claw_status claw_set_rows(claw_solver* s, int y0, int nrows, const double* rows, int on_device);
 
 /* Thread-local text of the last failure ("" if none). */

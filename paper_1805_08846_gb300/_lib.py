@@ -59,6 +59,8 @@ _SIGS = {
     "claw_conservation_sums": [_vp, _dp],
     "claw_get_rejections": [_vp, C.POINTER(C.c_long)],
     "claw_run_fixed_steps": [_vp, C.c_int, C.c_double, _dp],
+    "claw_checkpoint": [_vp],
+    "claw_rollback": [_vp],
     "claw_get_rows": [_vp, C.c_int, C.c_int, _vp, C.c_int],
     "claw_set_rows": [_vp, C.c_int, C.c_int, _vp, C.c_int],
     "claw_last_error": [],
@@ -209,6 +211,14 @@ def claw_run_fixed_steps(h, nsteps, dt):
     cfl = C.c_double(0.0)
     _check(lib().claw_run_fixed_steps(h, int(nsteps), float(dt), C.byref(cfl)), "claw_run_fixed_steps")
     return cfl.value
+
+
+def claw_checkpoint(h):
+    _check(lib().claw_checkpoint(h), "claw_checkpoint")
+
+
+def claw_rollback(h):
+    _check(lib().claw_rollback(h), "claw_rollback")
 
 
 def claw_get_rows(h, y0, out):

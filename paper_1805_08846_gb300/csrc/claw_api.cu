@@ -100,6 +100,10 @@ struct claw_solver {
     bool unsplit = false;
     std::vector<TileDesc> utiles;
     TileDesc* d_utiles = nullptr;
+    // claw_checkpoint: every field's kept version and the control blocks
+    void* ckpt = nullptr;
+    Control* ckpt_ctl = nullptr;
+    std::vector<int> ckpt_cur;   // kept slot of each (instance, field) at the checkpoint
 };
 
 namespace {
@@ -841,6 +845,8 @@ void claw_destroy(claw_solver* s) {
         if (s->d_order[d]) cudaFree(s->d_order[d]);
     }
     if (s->d_utiles) cudaFree(s->d_utiles);
+    if (s->ckpt) cudaFree(s->ckpt);
+    if (s->ckpt_ctl) cudaFree(s->ckpt_ctl);
     if (s->d_counters) cudaFree(s->d_counters);
     if (s->pool) cudaFree(s->pool);
     if (s->aux) cudaFree(s->aux);
@@ -901,6 +907,53 @@ claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* 
     if (cfl_peak)
         for (int i = 0; i < s->B; ++i) *cfl_peak = std::max(*cfl_peak, s->h_ctl[i].cfl_peak);
     return CLAW_OK;
+}
+
+// Element offset of (instance i, field f) inside the checkpoint buffer.
+static long long ckpt_offset(const claw_solver* s, int i, int f) {
+    long long off = 0;
+    for (int j = 0; j < i; ++j) off += (long long)s->m * s->inst[j].fstride;
+    return off + (long long)f * s->inst[i].fstride;
+}
+
+claw_status claw_checkpoint(claw_solver* s) {
+    CKS(check_solver(s));
+    if (!s->ckpt) {
+        long long elems = 0;
+        for (int i = 0; i < s->B; ++i) elems += (long long)s->m * s->inst[i].fstride;
+        CK(cudaMalloc(&s->ckpt, (size_t)elems * s->esize));
+        CK(cudaMalloc(&s->ckpt_ctl, sizeof(Control) * s->B));
+    }
+    CKS(read_ctl(s));                     // the kept slot of every field
+    s->ckpt_cur.assign((size_t)s->B * s->m, 0);
+    for (int i = 0; i < s->B; ++i)
+        for (int f = 0; f < s->m; ++f) {
+            const InstDesc& I = s->inst[i];
+            const int slot = s->h_ctl[i].cur[f];
+            s->ckpt_cur[(size_t)i * s->m + f] = slot;
+            const char* src = (const char*)s->pool + (I.offset + slot * I.vstride + f * I.fstride) * s->esize;
+            char* dst = (char*)s->ckpt + ckpt_offset(s, i, f) * s->esize;
+            CK(cudaMemcpyAsync(dst, src, (size_t)I.fstride * s->esize, cudaMemcpyDeviceToDevice, s->stream));
+        }
+    CK(cudaMemcpyAsync(s->ckpt_ctl, s->d_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToDevice, s->stream));
+    return latched_status(s, 0, s->B);
+}
+
+claw_status claw_rollback(claw_solver* s) {
+    CKS(check_solver(s));
+    if (!s->ckpt || s->ckpt_cur.empty()) return fail(CLAW_EINVAL, "no checkpoint to roll back to");
+    for (int i = 0; i < s->B; ++i)
+        for (int f = 0; f < s->m; ++f) {
+            const InstDesc& I = s->inst[i];
+            const int slot = s->ckpt_cur[(size_t)i * s->m + f];
+            char* dst = (char*)s->pool + (I.offset + slot * I.vstride + f * I.fstride) * s->esize;
+            const char* src = (const char*)s->ckpt + ckpt_offset(s, i, f) * s->esize;
+            CK(cudaMemcpyAsync(dst, src, (size_t)I.fstride * s->esize, cudaMemcpyDeviceToDevice, s->stream));
+        }
+    // the control blocks as they were: kept slots, clock, step counts, next step
+    CK(cudaMemcpyAsync(s->d_ctl, s->ckpt_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToDevice, s->stream));
+    CKS(read_ctl(s));
+    return latched_status(s, 0, s->B);
 }
 
 claw_status claw_run_steps(claw_solver* s, int nsteps) {

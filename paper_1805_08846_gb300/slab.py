@@ -246,13 +246,12 @@ class solver_stepper:
     are fixed (claw_run_fixed_steps; run_steps takes the CFL decision on the
     speeds of all ranks), rows cross through claw_get_rows /
     claw_set_rows as float64 torch tensors on `device` ("cpu" for gloo:
-    host tensors, copied), and the period's start is kept as a device copy
-    of the state for a redo."""
+    host tensors, copied), and the period's start is kept for a redo by
+    claw_checkpoint / claw_rollback."""
 
     def __init__(self, solver, device="cuda"):
         self.s = solver
         self.device = device
-        self._snap = None
         self._pending = []     # device rows whose copy may still be queued on the solver's stream
 
     def _sync(self, t):
@@ -280,13 +279,10 @@ class solver_stepper:
         return M
 
     def snapshot(self):
-        import torch
-        if self._snap is None:
-            self._snap = torch.empty(self.s.shape, dtype=torch.float64, device=self.device)
-        self.s.get_q(self._snap)
+        self.s.checkpoint()          # a device copy in the state's own precision
 
     def restore(self):
-        self.s.set_q(self._snap)
+        self.s.rollback()
 
     def run_fixed(self, n, dt) -> float:
         return float(self.s.run_fixed_steps(n, dt))

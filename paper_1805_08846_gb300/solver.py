@@ -91,6 +91,12 @@ class Solver:
         """nsteps kept steps of exactly dt; returns the largest Courant number."""
         return L.claw_run_fixed_steps(self.h, nsteps, dt)
 
+    def checkpoint(self):
+        L.claw_checkpoint(self.h)
+
+    def rollback(self):
+        L.claw_rollback(self.h)
+
     def get_rows(self, y0, out):
         return L.claw_get_rows(self.h, y0, out)
 

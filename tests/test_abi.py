@@ -90,4 +90,6 @@ def test_null_solver_is_rejected():
     assert lib.claw_run_fixed_steps(None, 2, 0.1, None) == L.CLAW_EINVAL
     assert lib.claw_get_rows(None, 0, 1, None, 0) == L.CLAW_EINVAL
     assert lib.claw_set_rows(None, 0, 1, None, 0) == L.CLAW_EINVAL
+    assert lib.claw_checkpoint(None) == L.CLAW_EINVAL
+    assert lib.claw_rollback(None) == L.CLAW_EINVAL
     lib.claw_destroy(None)

@@ -101,3 +101,27 @@ def test_rows_round_trip_and_fixed_steps_report_their_peak():
     assert max(oracle.rel_linf(got[f], ref[f]) for f in range(3)) <= 1e-12
     assert peak == pytest.approx(max(cfls), rel=1e-12)
 
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_checkpoint_and_rollback_are_bitwise(precision):
+    """claw_rollback returns to the checkpoint's state and clock exactly, and
+    the same steps taken again give the same result bit for bit."""
+    from paper_1805_08846_gb300 import ClawError
+    prob = problem("shallow_water", "unsplit", "periodic", shape=(64, 50))
+    with Solver.from_problem(prob, precision=precision) as s:
+        with pytest.raises(ClawError):
+            s.rollback()                         # nothing to roll back to yet
+        s.run_steps(2)
+        q0, t0 = s.get_q(), s.time()
+        s.checkpoint()
+        s.run_fixed_steps(3, 0.003)
+        q1, t1 = s.get_q(), s.time()
+        s.rollback()
+        np.testing.assert_array_equal(s.get_q(), q0)
+        assert s.time() == t0
+        s.run_fixed_steps(3, 0.003)
+        np.testing.assert_array_equal(s.get_q(), q1)
+        assert s.time() == t1
+        s.rollback()                             # the same checkpoint again
+        np.testing.assert_array_equal(s.get_q(), q0)
+
