@@ -60,9 +60,11 @@ class SlabLayout:
     def __post_init__(self):
         if self.P < 1 or self.H < 0:
             raise ValueError("need P >= 1 and H >= 0")
-        if any(self.rows(r)[1] - self.rows(r)[0] < max(self.H, 2) for r in range(self.P)):
+        # a neighbour's halo comes from one rank's owned rows (one rank: no halo)
+        need = max(self.H, 2) if self.P > 1 else 2
+        if any(self.rows(r)[1] - self.rows(r)[0] < need for r in range(self.P)):
             raise ValueError(f"{self.ny} rows over {self.P} ranks leave a slab thinner than "
-                             f"max(H, 2) = {max(self.H, 2)} rows")
+                             f"{need} rows")
 
     def rows(self, r: int):
         """Owned rows [lo, hi) of rank r (balanced, the first ny % P ranks one more)."""

@@ -92,6 +92,7 @@ def test_layout_covers_rows_and_windows_wrap():
     assert one.halos(0) == (0, 0) and one.y_bc(0, "periodic", "periodic") == ("periodic", "periodic")
     with pytest.raises(ValueError):
         S.SlabLayout(10, 4, 3, False)      # slabs of 2-3 rows cannot feed a 3-row halo
+    assert S.SlabLayout(10, 1, 16, False).halos(0) == (0, 0)   # one rank: the halo is unused
 
 
 class TensorStepper:
