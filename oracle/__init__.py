@@ -18,7 +18,8 @@ import numpy as np
 
 from . import build as _build
 
-_SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3}
+_SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3,
+            "shallow_water_dry": 4}
 _LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 _BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 _SPLITTINGS = {"godunov": 0, "strang": 1, "unsplit": 2}
@@ -33,7 +34,7 @@ class _Problem(C.Structure):
         ("rho", C.c_double), ("K", C.c_double), ("g", C.c_double),
         ("cfl_desired", C.c_double), ("cfl_max", C.c_double), ("dt_max", C.c_double),
         ("max_retries", C.c_int), ("rho_cell", _dp), ("K_cell", _dp),
-        ("splitting", C.c_int), ("B_cell", _dp),
+        ("splitting", C.c_int), ("B_cell", _dp), ("dry_tol", C.c_double),
     ]
 
 
@@ -68,6 +69,9 @@ def lib():
         L.orc_rp_shallow_water_bathy.restype = None
         L.orc_rp_shallow_water_bathy.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
                                                  _dp, _dp, _dp, _dp]
+        L.orc_rp_shallow_water_dry.restype = None
+        L.orc_rp_shallow_water_dry.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
+                                               C.c_double, _dp, _dp, _dp, _dp]
         L.orc_tr_acoustics.restype = None
         L.orc_tr_acoustics.argtypes = [_dp] + [C.c_double] * 6 + [_dp, _dp]
         L.orc_tr_shallow_water.restype = None
@@ -109,10 +113,11 @@ class Oracle:
             k = np.ascontiguousarray(prob.K_cell, dtype=np.float64)
             self._keep += [r, k]
             P.rho_cell, P.K_cell = _ptr(r), _ptr(k)
-        if prob.system == "shallow_water_bathy":
+        if prob.system in ("shallow_water_bathy", "shallow_water_dry"):
             b = np.ascontiguousarray(prob.B_cell, dtype=np.float64)
             self._keep.append(b)
             P.B_cell = _ptr(b)
+        P.dry_tol = float(getattr(prob, "dry_tol", 0.0))
         self.P = P
         self.m = 3 if prob.system.startswith("shallow_water") else prob.ndim + 1
         self.shape = (self.m,) + tuple(reversed(prob.n))
@@ -165,9 +170,10 @@ class Oracle:
         return self._run(q, 1, 0, t_final, fixed_dt, t, dt)
 
 
-def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81, B_l=0.0, B_r=0.0):
-    """Waves W[p][c] (f-waves for shallow_water_bathy), speeds s[p], A-dQ, A+dQ
-    at one interface (reduced states)."""
+def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81, B_l=0.0, B_r=0.0,
+            dry_tol=1e-3):
+    """Waves W[p][c] (f-waves for shallow_water_bathy and shallow_water_dry),
+    speeds s[p], A-dQ, A+dQ at one interface (reduced states)."""
     ql = np.ascontiguousarray(np.pad(np.asarray(ql, dtype=np.float64), (0, 3 - len(ql))))
     qr = np.ascontiguousarray(np.pad(np.asarray(qr, dtype=np.float64), (0, 3 - len(qr))))
     W = np.zeros((3, 3))
@@ -181,6 +187,10 @@ def riemann(system: str, ql, qr, rho_l=1.0, K_l=1.0, rho_r=1.0, K_r=1.0, g=9.81,
     if system == "shallow_water_bathy":
         lib().orc_rp_shallow_water_bathy(_ptr(ql), _ptr(qr), float(B_l), float(B_r), float(g),
                                          _ptr(W), _ptr(s), _ptr(am), _ptr(ap))
+        return W, s, am, ap
+    if system == "shallow_water_dry":
+        lib().orc_rp_shallow_water_dry(_ptr(ql), _ptr(qr), float(B_l), float(B_r), float(g),
+                                       float(dry_tol), _ptr(W), _ptr(s), _ptr(am), _ptr(ap))
         return W, s, am, ap
     lib().orc_rp_acoustics(_ptr(ql), _ptr(qr), float(rho_l), float(K_l), float(rho_r),
                            float(K_r), _ptr(W), _ptr(s), _ptr(am), _ptr(ap))

@@ -33,8 +33,11 @@ extern "C" {
 
 /* ORC_SHALLOW_WATER_BATHY: shallow water over a bottom elevation B per
  * cell, in the f-wave form (the returned "waves" are f-waves Z_p, and the
- * correction term uses sign(s_p) instead of |s_p|). */
-enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2, ORC_SHALLOW_WATER_BATHY = 3 };
+ * correction term uses sign(s_p) instead of |s_p|).  ORC_SHALLOW_WATER_DRY:
+ * shallow water over B with wetting and drying (cells with h <= dry_tol are
+ * dry), HLLE waves; see orc_rp_shallow_water_dry. */
+enum { ORC_ACOUSTICS = 0, ORC_ACOUSTICS_VAR = 1, ORC_SHALLOW_WATER = 2, ORC_SHALLOW_WATER_BATHY = 3,
+       ORC_SHALLOW_WATER_DRY = 4 };
 /* ORC_LIM_NONE: unlimited second-order correction (Lax-Wendroff);
  * ORC_LIM_FIRST_ORDER: no correction at all (Godunov's first-order upwind
  * method: the Riemann solution and the fluctuation update alone). */
@@ -62,7 +65,8 @@ typedef struct {
     const double *rho_cell;/* per-cell rho, K (ORC_ACOUSTICS_VAR), else NULL */
     const double *K_cell;
     int splitting;         /* ORC_SPLIT_* */
-    const double *B_cell;  /* bottom elevation per cell (ORC_SHALLOW_WATER_BATHY), else NULL */
+    const double *B_cell;  /* bottom elevation per cell (ORC_SHALLOW_WATER_BATHY / _DRY), else NULL */
+    double dry_tol;        /* ORC_SHALLOW_WATER_DRY: a cell with h <= dry_tol is dry */
 } orc_problem;
 
 /* Number of state fields m and waves mwaves for a problem. */
@@ -80,6 +84,12 @@ void orc_rp_shallow_water(const double *ql, const double *qr, double g,
 void orc_rp_shallow_water_bathy(const double *ql, const double *qr, double B_l, double B_r,
                                 double g, double W[3][3], double s[3], double amdq[3],
                                 double apdq[3]);
+
+/* HLLE waves of the wet/dry bathymetry system (see orc_shallow_water.c);
+ * zero waves (but not fluctuations) at an interface with a dry side. */
+void orc_rp_shallow_water_dry(const double *ql, const double *qr, double B_l, double B_r,
+                              double g, double dry_tol, double W[3][3], double s[3],
+                              double amdq[3], double apdq[3]);
 
 /* Wave limiter function phi(theta), minmod or MC; ORC_LIM_NONE gives 1. */
 double orc_phi(int limiter, double theta);

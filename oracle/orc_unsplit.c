@@ -187,7 +187,8 @@ static void transverse(const orc_problem *P, const padded *u, int d, int i, int 
 int orc_unsplit_step(const orc_problem *P, const double *qin, double *qout, double dt,
                      double m_d[3])
 {
-    if (P->ndim != 2 || P->system == ORC_SHALLOW_WATER_BATHY) return -1;
+    if (P->ndim != 2 || P->system == ORC_SHALLOW_WATER_BATHY || P->system == ORC_SHALLOW_WATER_DRY)
+        return -1;
     int nx = P->n[0], ny = P->n[1];
     long ncell = (long)nx * ny;
     int nw = orc_mwaves(P);

@@ -32,7 +32,14 @@
 
 static int is_sw(const orc_problem *P)
 {
-    return P->system == ORC_SHALLOW_WATER || P->system == ORC_SHALLOW_WATER_BATHY;
+    return P->system == ORC_SHALLOW_WATER || P->system == ORC_SHALLOW_WATER_BATHY ||
+           P->system == ORC_SHALLOW_WATER_DRY;
+}
+
+/* Systems whose Riemann solver returns f-waves over a bottom elevation. */
+static int has_bed(const orc_problem *P)
+{
+    return P->system == ORC_SHALLOW_WATER_BATHY || P->system == ORC_SHALLOW_WATER_DRY;
 }
 
 int orc_m(const orc_problem *P)
@@ -133,6 +140,8 @@ static void riemann(const orc_problem *P, const double *ql, const double *qr,
         orc_rp_shallow_water(ql, qr, P->g, W, s, amdq, apdq);
     else if (P->system == ORC_SHALLOW_WATER_BATHY)
         orc_rp_shallow_water_bathy(ql, qr, B_l, B_r, P->g, W, s, amdq, apdq);
+    else if (P->system == ORC_SHALLOW_WATER_DRY)
+        orc_rp_shallow_water_dry(ql, qr, B_l, B_r, P->g, P->dry_tol, W, s, amdq, apdq);
     else
         orc_rp_acoustics(ql, qr, rho_l, K_l, rho_r, K_r, W, s, amdq, apdq);
 }
@@ -187,7 +196,7 @@ static void gather_line(const orc_problem *P, int d, long line, const double *qi
             double v = qin[(long)field_of(P, d, c) * ncell + idx];
             w->q[i + 2][c] = (c == 1) ? sign * v : v;
         }
-        w->B[i + 2] = P->system == ORC_SHALLOW_WATER_BATHY ? P->B_cell[idx] : 0.0;
+        w->B[i + 2] = has_bed(P) ? P->B_cell[idx] : 0.0;
         if (P->system == ORC_ACOUSTICS_VAR) {
             w->rho[i + 2] = P->rho_cell[idx];
             w->K[i + 2] = P->K_cell[idx];

@@ -23,7 +23,7 @@ import numpy as np
 
 SEED = 1805
 
-SYSTEMS = ("acoustics", "acoustics_var", "shallow_water", "shallow_water_bathy")
+SYSTEMS = ("acoustics", "acoustics_var", "shallow_water", "shallow_water_bathy", "shallow_water_dry")
 LIMITERS = ("none", "minmod", "mc", "first_order")
 BCS = ("periodic", "extrap", "wall")
 SPLITTINGS = ("godunov", "strang", "unsplit")
@@ -51,10 +51,11 @@ class Problem:
     K_cell: Optional[np.ndarray] = None
     name: str = ""
     splitting: str = "godunov"    # one of SPLITTINGS
-    B_cell: Optional[np.ndarray] = None     # (ny, nx) bottom elevation for shallow_water_bathy
+    B_cell: Optional[np.ndarray] = None     # (ny, nx) bottom elevation (shallow_water_bathy / _dry)
     # cell widths given exactly (a piece of a larger grid keeps its parent's
     # widths; recomputing them from the piece's bounds can differ in the last bit)
     cell_width: Optional[tuple] = None
+    dry_tol: float = 1e-3         # shallow_water_dry: a cell with h <= dry_tol is dry
 
     @property
     def m(self) -> int:
@@ -121,6 +122,29 @@ def sw_radial_dam_break(n: int = 4096, ny: Optional[int] = None, limiter: str = 
                    (bc,) * 4, q0, g=9.81, nsteps=nsteps, name=f"sw_radial_dam_break_{n}x{ny}")
 
 
+def sw_transonic_dam_break(n: int = 120, width: int = 4, axis: int = 0, mirror: bool = False,
+                           limiter: str = "mc", h_deep: float = 1.0, h_shallow: float = 0.1,
+                           bc: str = "extrap") -> Problem:
+    """Planar dam break on [-1,1]^2 whose rarefaction fan spans the jump's
+    position: h = h_deep on one side of 0 and h_shallow on the other (depth
+    ratio 10), zero momentum.  The jump runs across direction `axis` (n cells
+    along it, `width` uniform cells across).  mirror=False puts the deep side
+    at negative coordinates, so the 1-wave fan is transonic; mirror=True puts
+    it at positive coordinates (the 3-wave fan is transonic)."""
+    c = centres(n, -1.0, 1.0)
+    prof = np.where(c > 0.0, h_deep, h_shallow) if mirror else np.where(c < 0.0, h_deep, h_shallow)
+    if axis == 0:
+        shape_xy = (n, width)
+        h = np.broadcast_to(prof[None, :], (width, n))
+    else:
+        shape_xy = (width, n)
+        h = np.broadcast_to(prof[:, None], (n, width))
+    q0 = np.zeros((3,) + h.shape)
+    q0[0] = h
+    return Problem(2, shape_xy, (-1.0, -1.0), (1.0, 1.0), "shallow_water", limiter, (bc,) * 4,
+                   q0, name=f"sw_transonic_{'xy'[axis]}{'_mirror' if mirror else ''}_{n}")
+
+
 def sw_bathymetry(n: int = 4096, limiter: str = "minmod", bc: str = "extrap", nsteps: int = 200,
                   bump: float = 0.5, hump: float = 0.2) -> Problem:
     """Shallow water over bathymetry on [-1,1]^2: a Gaussian seamount
@@ -137,6 +161,67 @@ def sw_bathymetry(n: int = 4096, limiter: str = "minmod", bc: str = "extrap", ns
     q0[0] = eta - B
     return Problem(2, (n, n), (-1.0, -1.0), (1.0, 1.0), "shallow_water_bathy", limiter,
                    (bc,) * 4, q0, nsteps=nsteps, B_cell=B, name=f"sw_bathymetry_{n}")
+
+
+def _round24(a: np.ndarray) -> np.ndarray:
+    """Values rounded to multiples of 2^-24 (exact in FP32 for |a| < 1, and
+    their differences are exact), so h = eta - B and eta = h + B are exact."""
+    q = 2.0 ** -24
+    return np.round(np.asarray(a, dtype=np.float64) / q) * q
+
+
+def sw_dry_dam_break(n: int = 200, width: int = 4, axis: int = 0, h_l: float = 1.0,
+                     limiter: str = "mc", bc: str = "extrap") -> Problem:
+    """Ritter's dam break on [-1,1]^2: depth h_l at negative coordinates along
+    `axis`, a dry bed (h = 0) at positive ones, flat bottom B = 0, zero
+    momentum; n cells along `axis`, `width` uniform cells across.  System
+    shallow_water_dry (wetting and drying)."""
+    c = centres(n, -1.0, 1.0)
+    prof = np.where(c < 0.0, h_l, 0.0)
+    if axis == 0:
+        shape_xy, h = (n, width), np.broadcast_to(prof[None, :], (width, n))
+    else:
+        shape_xy, h = (width, n), np.broadcast_to(prof[:, None], (n, width))
+    q0 = np.zeros((3,) + h.shape)
+    q0[0] = h
+    return Problem(2, shape_xy, (-1.0, -1.0), (1.0, 1.0), "shallow_water_dry", limiter, (bc,) * 4,
+                   q0, B_cell=np.zeros(h.shape), name=f"sw_ritter_{'xy'[axis]}_{n}")
+
+
+def sw_island(n: int = 4096, ny: Optional[int] = None, limiter: str = "minmod", bc: str = "wall",
+              hump: float = 0.2, peak: float = 1.6, nsteps: int = 200) -> Problem:
+    """Wetting and drying on [-1,1]^2: a lake whose surface rests at eta = 1
+    around an island B = peak exp(-8 ((x - 0.25)^2 + y^2)) that rises above
+    it (the island's top, where B > eta, is dry: h = 0), with a Gaussian
+    surface hump eta = 1 + hump exp(-40 ((x + 0.5)^2 + y^2)) that runs up the
+    island's shore and falls back; zero momentum.  B and eta are rounded to
+    multiples of 2^-24, so h = max(eta - B, 0) is exact and, with hump = 0,
+    the lake is exactly at rest."""
+    ny = n if ny is None else ny
+    x = centres(n, -1.0, 1.0)
+    y = centres(ny, -1.0, 1.0)
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    B = _round24(peak * np.exp(-8.0 * ((X - 0.25) ** 2 + Y ** 2)))
+    eta = 1.0 + _round24(hump * np.exp(-40.0 * ((X + 0.5) ** 2 + Y ** 2)))
+    q0 = np.zeros((3, ny, n))
+    q0[0] = np.maximum(eta - B, 0.0)
+    return Problem(2, (n, ny), (-1.0, -1.0), (1.0, 1.0), "shallow_water_dry", limiter, (bc,) * 4,
+                   q0, nsteps=nsteps, B_cell=B, name=f"sw_island_{n}x{ny}")
+
+
+def sw_beach(n: int = 200, ny: int = 40, limiter: str = "mc", bc: str = "wall",
+             slope: float = 0.8, eta0: float = 0.3, hump: float = 0.15) -> Problem:
+    """Run-up on a plane beach on [-1,1]^2: bottom B = slope * x, still water
+    at eta0 (dry where B > eta0) with a hump eta0 + hump exp(-30 (x + 0.4)^2),
+    uniform across y, zero momentum; walls by default (mass is conserved
+    exactly).  B and eta are rounded to multiples of 2^-24."""
+    x = centres(n, -1.0, 1.0)
+    B = _round24(np.broadcast_to(slope * x[None, :], (ny, n)))
+    eta = eta0 + _round24(np.broadcast_to(hump * np.exp(-30.0 * (x[None, :] + 0.4) ** 2), (ny, n)))
+    q0 = np.zeros((3, ny, n))
+    q0[0] = np.maximum(eta - B, 0.0)
+    return Problem(2, (n, ny), (-1.0, -1.0), (1.0, 1.0), "shallow_water_dry", limiter, (bc,) * 4,
+                   q0, B_cell=B.copy(), name=f"sw_beach_{n}x{ny}")
 
 
 def acoustics_3d_layers(n: int = 512, width: float = 200.0, limiter: str = "mc",
@@ -294,6 +379,21 @@ def random_problem(system: str, shape_xyz: Sequence[int], limiter: str, bc,
     if system == "shallow_water_bathy":
         # smooth random bottom within [-0.2, 0.2] (the depth stays > 0.2)
         B_cell = 0.6 * random_smooth_state("acoustics", arr_shape, seed=seed + 11, amplitude=0.1)[0]
+    if system == "shallow_water_dry":
+        # the same random bottom plus a ridge that rises above the surface:
+        # q0[0] is read as the surface eta, the depth is max(eta - B, 0) (dry
+        # cells on and around the ridge), velocities q0[1], q0[2] where wet
+        rng = np.random.Generator(np.random.PCG64(seed + 13))
+        cx, cy = rng.uniform(0.3, 0.7, size=2)
+        coords = np.meshgrid(*[centres(s_, 0.0, 1.0) for s_ in arr_shape], indexing="ij")
+        r2 = (coords[-1] - cx) ** 2 + (coords[-2] - cy) ** 2
+        B_cell = _round24(0.6 * random_smooth_state("acoustics", arr_shape, seed=seed + 11,
+                                                   amplitude=0.1)[0] + 2.5 * np.exp(-30.0 * r2))
+        eta = _round24(q0[0])
+        h = np.maximum(eta - B_cell, 0.0)
+        q0[1] = q0[1] * h
+        q0[2] = q0[2] * h
+        q0[0] = h
     return Problem(ndim, tuple(shape_xyz), (0.0,) * ndim, (1.0,) * ndim, system, limiter,
                    tuple(bc), q0, rho=1.0, K=4.0, rho_cell=rho_cell, K_cell=K_cell, B_cell=B_cell,
                    name=f"{system}_{'x'.join(map(str, shape_xyz))}_{limiter}")

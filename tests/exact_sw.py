@@ -45,3 +45,18 @@ def dam_break_profile(x, t, h_l, h_r, x0=0.0, g=9.81):
     h[mid], u[mid] = st["h_m"], st["u_m"]
     h[right], u[right] = h_r, 0.0
     return h, h * u
+
+
+def ritter_profile(x, t, h_l, x0=0.0, g=9.81):
+    """Ritter's dam break onto a dry bed (h_l, 0) | (0, 0), flat bottom, t > 0:
+    still water left of xi = -c_l, the fan h = (2 c_l - xi)^2 / (9 g),
+    u = 2 (c_l + xi) / 3 for -c_l < xi < 2 c_l (c_l = sqrt(g h_l)), dry beyond
+    the front xi = 2 c_l.  Returns (h, hu)."""
+    c_l = np.sqrt(g * h_l)
+    xi = (np.asarray(x, dtype=np.float64) - x0) / t
+    fan = (xi > -c_l) & (xi < 2.0 * c_l)
+    h = np.where(xi <= -c_l, h_l, 0.0)
+    u = np.zeros_like(xi)
+    h[fan] = (2.0 * c_l - xi[fan]) ** 2 / (9.0 * g)
+    u[fan] = 2.0 * (c_l + xi[fan]) / 3.0
+    return h, h * u

@@ -87,6 +87,19 @@ MUTANTS = [
     ("orc_unsplit.c", "if (I - 1 >= 0) for (int c = 0; c < 3; ++c) fl[3 * (d * np + pidx(&u, il, jl)) + c] += fa[c];",
      "if (I - 1 >= 0) for (int c = 0; c < 3; ++c) fl[3 * (d * np + pidx(&u, il, jl)) + c] += fb[c];",
      "left fluctuation taken from the wrong side"),
+    # wetting and drying (hydrostatic reconstruction around HLLE)
+    ("orc_shallow_water.c", "double lam_rp = wet_r ? u_r + c_r : u_l + 2.0 * c_l;",
+     "double lam_rp = wet_r ? u_r + c_r : u_l + c_l;", "dry-bed front at u + c instead of u + 2c"),
+    ("orc_shallow_water.c", "double Bs = B_l > B_r ? B_l : B_r;",
+     "double Bs = B_l < B_r ? B_l : B_r;", "reconstruction against the lower bed"),
+    ("orc_shallow_water.c", "amdq[c] = (hl - h_l) * cut_l[c];", "amdq[c] = 0.0;",
+     "momentum the reconstruction removes is lost"),
+    ("orc_shallow_water.c", "double s1 = u_hat - c_hat < lam_lm ? u_hat - c_hat : lam_lm;",
+     "double s1 = u_hat - c_hat;", "Roe speed instead of Einfeldt's"),
+    ("orc_shallow_water.c", "    if (!wet_l || !wet_r)\n        for (int p = 0; p < 3; ++p)",
+     "    if (0)\n        for (int p = 0; p < 3; ++p)", "correction kept at the shoreline"),
+    ("orc_shallow_water.c", "W[2][c] = (df - s1 * dq) / (s3 - s1);",
+     "W[2][c] = (df - s3 * dq) / (s3 - s1);", "HLL wave with the wrong speed"),
 ]
 
 
@@ -121,6 +134,7 @@ def test_pins_catch_planted_mistake(tmp_path, mutant):
     lib = _build_mutant(str(tmp_path), fname, old, new, *mutant[4:])
     env = dict(os.environ, ORC_LIB=lib, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_dry_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the mutant: {what}\n{r.stdout[-2000:]}"
