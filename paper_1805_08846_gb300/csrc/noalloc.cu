@@ -5,8 +5,9 @@
 // Scratch: g_speed_partials holds one partial maximum (the bits of a
 // non-negative double) per CTA and direction.  Every CTA writes its slot
 // before the reduce kernel reads it, so nothing needs clearing; the array
-// keeps the last call's values, and two calls that overlap on the GPU (on
-// different streams) race on it.
+// keeps the last call's values.  Each device that loads the library has its
+// own copy of the array, so calls on different devices never meet; two calls
+// that overlap on the same device (on different streams) race on it.
 #include <claw.h>
 
 #include <float.h>
@@ -104,18 +105,36 @@ __global__ void __launch_bounds__(kNaLines) na_speed_kernel(const double* q, con
     }
 }
 
-// M = max_d (max|s|_d / dx_d) from the partials, one thread.
-__global__ void na_reduce_kernel(const unsigned long long* partials, NaGeom G, int nblk0, int nblk1,
-                                 int nblk2, double* out) {
+// M = max_d (max|s|_d / dx_d) from the partials: one CTA, each thread a
+// strided subset of every direction's partials, then warp and CTA maxima
+// (integer maxima of the bit patterns: exact, so the order does not matter).
+constexpr int kNaReduceThreads = 512;
+
+__global__ void __launch_bounds__(kNaReduceThreads) na_reduce_kernel(const unsigned long long* partials,
+                                                                     NaGeom G, int nblk0, int nblk1,
+                                                                     int nblk2, double* out) {
     const int nblk[3] = {nblk0, nblk1, nblk2};
+    __shared__ unsigned long long warp_max[3][kNaReduceThreads / 32];
+    for (int d = 0; d < G.ndim; ++d) {
+        unsigned long long b = 0ull;
+        for (int i = threadIdx.x; i < nblk[d]; i += kNaReduceThreads) {
+            const unsigned long long v = partials[d * kNaMaxCtasPerDir + i];
+            b = v > b ? v : b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+            b = v > b ? v : b;
+        }
+        if ((threadIdx.x & 31) == 0) warp_max[d][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double M = 0.0;
     bool nonfinite = false;
     for (int d = 0; d < G.ndim; ++d) {
         unsigned long long b = 0ull;
-        for (int i = 0; i < nblk[d]; ++i) {
-            const unsigned long long v = partials[d * kNaMaxCtasPerDir + i];
-            b = v > b ? v : b;
-        }
+        for (int w = 0; w < kNaReduceThreads / 32; ++w) b = warp_max[d][w] > b ? warp_max[d][w] : b;
         const double md = __longlong_as_double((long long)b);
         if (!(md <= DBL_MAX)) nonfinite = true;
         const double v = md / G.dx[d];
@@ -158,7 +177,7 @@ cudaError_t na_launch(const double* q, const double* rho, const double* K, const
     if (G.ndim == 3) {
         if constexpr (Sys::NQ == 2) na_speed_kernel<Sys, 2><<<nblk[2], kNaLines, 0, st>>>(q, rho, K, G, P, scratch);
     }
-    na_reduce_kernel<<<1, 1, 0, st>>>(scratch, G, nblk[0], nblk[1], nblk[2], out);
+    na_reduce_kernel<<<1, kNaReduceThreads, 0, st>>>(scratch, G, nblk[0], nblk[1], nblk[2], out);
     return cudaGetLastError();
 }
 

@@ -125,3 +125,21 @@ def test_checkpoint_and_rollback_are_bitwise(precision):
         s.rollback()                             # the same checkpoint again
         np.testing.assert_array_equal(s.get_q(), q0)
 
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_a_period_whose_courant_number_exceeds_cfl_max_is_redone_on_the_gpu(precision):
+    """A radial dam break speeds up as its shock forms: a period of four steps
+    at dt = 0.9 / M(start) reaches a Courant number above 1, so the slab loop
+    rolls every slab back to its checkpoint (claw_rollback, halo rows
+    included) and redoes the period with a smaller step.  The result equals
+    one Solver over the whole grid taking the same steps (FP64 to 1e-12, FP32
+    bit for bit: the same kernels on the same data)."""
+    prob = inputs.sw_radial_dam_break(64, ny=60)
+    q, info = decomposed(prob, 2, k=4, nsteps=8, precision=precision)
+    assert info.redone > 0, info
+    ref = whole(prob, info.dts, precision)
+    if precision == 64:
+        assert max(oracle.rel_linf(q[f], ref[f]) for f in range(3)) <= 1e-12
+    else:
+        np.testing.assert_array_equal(q, ref)

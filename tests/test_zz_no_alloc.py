@@ -1,16 +1,18 @@
-"""The CFL speed pass that allocates nothing, checked against claw_max_speed.
+"""The CFL speed pass that allocates nothing, checked against the oracle and claw_max_speed.
 
 claw_max_speed_noalloc serves callers that cannot allocate device memory --
 a framework that owns every byte of device memory through its own pool, or
 a loop where an allocation could synchronise the device -- but hold their
 state on the GPU already.  It keeps its scratch in a fixed array inside the
-library, shared by all calls.  Its result must equal the solver-based
-claw_max_speed (same tolerance as the other FP64 parity tests), on two calls
-in a row: the second call runs on the scratch the first one left behind.
+library, shared by all calls on a device.  Its result must equal the
+oracle's CFL speed max_d(max|s| / dx_d) of the same state and the
+solver-based claw_max_speed (same tolerance as the other FP64 parity tests),
+on calls in a row: each call runs on the scratch the one before left behind.
 """
 import numpy as np
 import pytest
 
+from oracle import Oracle
 from paper_1805_08846_gb300 import Solver, inputs
 from paper_1805_08846_gb300 import _lib as L
 
@@ -39,17 +41,23 @@ def _noalloc_value(torch, prob, stream):
     return float(out.item())
 
 
-def test_noalloc_speed_pass_matches_claw_max_speed_on_two_calls_in_a_row():
+def test_noalloc_speed_pass_matches_the_oracle_and_claw_max_speed_on_calls_in_a_row():
     torch = pytest.importorskip("torch")
     stream = torch.cuda.Stream()
-    first = inputs.sw_radial_dam_break(300, ny=211)
-    second = inputs.random_problem("acoustics_var", (37, 29, 23), "mc",
-                                   ("wall", "periodic", "extrap", "wall", "periodic", "wall"))
-    for prob in (first, second):
-        want = _solver_value(prob)
+    # shallow water, variable-coefficient 3D acoustics, constant-coefficient
+    # acoustics (2D and 3D): every solver branch of the speed pass, each call
+    # on the scratch the previous one left behind
+    probs = [inputs.sw_radial_dam_break(300, ny=211),
+             inputs.random_problem("acoustics_var", (37, 29, 23), "mc",
+                                   ("wall", "periodic", "extrap", "wall", "periodic", "wall")),
+             inputs.acoustics_2d_pulse(130, ny=70, K=4.0),
+             inputs.random_problem("acoustics", (21, 19, 33), "mc", "periodic")]
+    for prob in probs:
+        want = Oracle(prob).max_speed_over_dx(prob.q0)
         with torch.cuda.stream(stream):
             got = _noalloc_value(torch, prob, stream)
         assert abs(got - want) <= TOL64 * abs(want), (prob.name, got, want)
+        assert abs(got - _solver_value(prob)) <= TOL64 * abs(want), prob.name
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
