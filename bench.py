@@ -244,6 +244,34 @@ def extra_bathymetry(args, peak_gbs):
     return out
 
 
+def extra_dry(args, peak_gbs):
+    """Shallow water with wetting and drying (hydrostatic reconstruction
+    around HLLE) on a 4096^2 lake around an emerged island, a surface hump
+    running up its shore, walls: FP32 and FP64 cell-updates/s and the HBM
+    fraction of the dominant FP32 sweep (7 values of 4 B per cell and sweep:
+    h, hu, hv read and written, B read)."""
+    from paper_1805_08846_gb300 import Solver, inputs
+    prob = inputs.sw_island(args.n)
+    out = {"workload": f"2D shallow water with wetting and drying, {args.n}^2 lake around an "
+                       f"emerged island, hump running up its shore, minmod, walls, CFL 0.9"}
+    for prec, steps in ((32, 100), (64, 5)):
+        s = Solver.from_problem(prob, precision=prec, stream="torch")
+        seg = s.autotune(2)
+        s.run_steps(3)
+        ms, tot, nl = s.profile_steps(steps)          # per-sweep breakdown
+        step_ms = graph_ms_per_step(s, prob, steps)
+        s.close()
+        r = {"value": prob.ncells / (step_ms * 1e-3), "ms_per_step": step_ms,
+             "sweep_ms": ms[:2], "steps": steps, "segments": seg[:2]}
+        if prec == 32:
+            dom = int(np.argmax(ms[:2]))
+            ach = 28 * prob.ncells / (ms[dom] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+                             "frac": ach / peak_gbs, "kernel": f"sweep dir={'xy'[dom]}"}
+        out[f"f{prec}"] = r
+    return out
+
+
 def extra_unsplit(args, peak_gbs):
     """The unsplit update with transverse waves on the 4096^2 radial dam
     break (minmod, outflow): FP32 and FP64 cell-updates/s of the one kernel
@@ -450,9 +478,12 @@ def accuracy(args):
     return 0
 
 
-def extra_ensembles(args):
+def extra_ensembles(args, peak_gbs):
     """Batched FP32 ensembles (one launch per sweep for all instances) against
-    the plain FP64 path run instance by instance on the same instances."""
+    the plain FP64 path run instance by instance on the same instances; the
+    batched sweeps' times and the HBM fraction of the dominant one (24 B per
+    cell and sweep in both: shallow water h, hu, hv read and written; 3D
+    acoustics p, u_d read and written, Z, c read)."""
     from paper_1805_08846_gb300 import Ensemble, Solver, inputs
     res = {}
     for name, gen, steps32, steps64 in (
@@ -460,12 +491,15 @@ def extra_ensembles(args):
             ("acoustics3d_64", lambda: inputs.acoustics3d_ensemble(), 100, 3)):
         probs = gen()
         cells = sum(p.ncells for p in probs)
+        ndim = probs[0].ndim
         e = Ensemble.from_problems(probs, precision=32)
         seg = e.autotune(1)
         e.run_steps(3)
         ms, tot, nl = e.profile_steps(steps32)
         e.close()
         v32 = cells * steps32 / (tot * 1e-3)
+        dom = int(np.argmax(ms[:ndim]))
+        ach = 24 * cells / (ms[dom] * 1e-3) / 1e9
         t64 = 0.0
         for p in probs:
             s = Solver.from_problem(p, precision=64)
@@ -476,7 +510,11 @@ def extra_ensembles(args):
         v64 = cells * steps64 / (t64 * 1e-3)
         res[name] = {"instances": len(probs), "cells": cells, "fp32_batched": v32,
                      "fp32_steps": steps32, "fp64_per_instance": v64, "fp64_steps": steps64,
-                     "ratio": v32 / v64, "segments": seg, "unit": METRIC}
+                     "ratio": v32 / v64, "segments": seg, "unit": METRIC,
+                     "sweep_ms": ms[:ndim],
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+                                  "frac": ach / peak_gbs, "kernel": f"batched sweep dir={'xyz'[dom]}"},
+                     "step_hbm_frac": 24 * ndim * v32 / 1e9 / peak_gbs}
         del probs
     return res
 
@@ -608,7 +646,7 @@ def main():
                          "slab: one grid split along y across the ranks (strong scaling)")
     ap.add_argument("--period", type=int, default=8, help="with --decomp slab: steps per halo refresh")
     ap.add_argument("--only-extra", default=None,
-                    choices=["acoustics3d", "sw_bathymetry", "sw_unsplit", "ensembles"],
+                    choices=["acoustics3d", "sw_bathymetry", "sw_dry", "sw_unsplit", "ensembles"],
                     help="run one extra measurement alone and print it")
     ap.add_argument("--fixed-segments", action="store_true",
                     help="with --paper-tables: 64-cell segments, no autotuning (for ncu)")
@@ -623,8 +661,8 @@ def main():
         import torch
         torch.cuda.set_device(0)
         peak_gbs, _ = load_peaks()
-        fn = {"acoustics3d": extra_acoustics3d, "sw_bathymetry": extra_bathymetry,
-              "sw_unsplit": extra_unsplit, "ensembles": lambda a, p: extra_ensembles(a)}[args.only_extra]
+        fn = {"acoustics3d": extra_acoustics3d, "sw_bathymetry": extra_bathymetry, "sw_dry": extra_dry,
+              "sw_unsplit": extra_unsplit, "ensembles": extra_ensembles}[args.only_extra]
         print(json.dumps({args.only_extra: fn(args, peak_gbs)}), flush=True)
         return 0
     if args.paper_tables or args.size_scaling or args.accuracy:
@@ -754,8 +792,9 @@ def main():
     if not args.no_extras and rank == 0:
         for key, fn in (("acoustics3d", lambda: extra_acoustics3d(args, peak_gbs)),
                         ("sw_bathymetry", lambda: extra_bathymetry(args, peak_gbs)),
+                        ("sw_dry", lambda: extra_dry(args, peak_gbs)),
                         ("sw_unsplit", lambda: extra_unsplit(args, peak_gbs)),
-                        ("ensembles", lambda: extra_ensembles(args))):
+                        ("ensembles", lambda: extra_ensembles(args, peak_gbs))):
             try:
                 extras[key] = fn()
             except Exception as exc:    # recorded, the main line still prints

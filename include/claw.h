@@ -27,6 +27,16 @@
  *                       the Roe eigenvectors (Sec. 3's Clawpack base adds
  *                       source terms to the hyperbolic part), so a lake at
  *                       rest stays exactly at rest; no entropy fix, h > 0.
+ *   CLAW_SHALLOW_WATER_DRY  the same over B with wetting and drying: a cell
+ *                       with h <= claw_params.dry_tol is dry (h = 0 allowed).
+ *                       Each interface reconstructs the depths hydrostatically
+ *                       against max(B_l, B_r) and solves the flat problem by
+ *                       HLLE (Einfeldt's speeds, dry-bed front speed u -/+ 2c);
+ *                       no second-order correction at the shoreline.  Mass is
+ *                       conserved, a lake at rest (also around an emerged
+ *                       island) stays exactly at rest, h stays >= 0.  The paper
+ *                       is silent on dry states: this is the library's reading
+ *                       of Sec. 3's source terms for them.
  *
  * Conventions for every call:
  *   - State arrays crossing the boundary are FP64, structure of arrays,
@@ -63,7 +73,8 @@ typedef enum {
     CLAW_ENOMEM = 2,     /* device or pinned host allocation failed */
     CLAW_ECUDA = 3,      /* a CUDA runtime call failed (message in claw_last_error) */
     CLAW_ECFL = 4,       /* more than max_retries consecutive CFL rejections */
-    CLAW_ENONPHYS = 5,   /* NaN / Inf in the state, or h <= 0 (shallow water) */
+    CLAW_ENONPHYS = 5,   /* NaN / Inf in the state, or h <= 0 (shallow water; h < 0 with
+                            wetting and drying) */
     CLAW_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
     CLAW_EBOUNDS = 7     /* a size or index outside the supported range */
 } claw_status;
@@ -73,7 +84,8 @@ typedef enum {
     CLAW_ACOUSTICS = 0,
     CLAW_ACOUSTICS_VAR = 1,
     CLAW_SHALLOW_WATER = 2,
-    CLAW_SHALLOW_WATER_BATHY = 3
+    CLAW_SHALLOW_WATER_BATHY = 3,
+    CLAW_SHALLOW_WATER_DRY = 4
 } claw_system;
 /* Second-order correction of Sec. 3 Eq. LW-update: NONE applies it
  * unlimited (Lax-Wendroff), MINMOD / MC limit each wave against its upwind
@@ -95,7 +107,7 @@ typedef struct { int ndim; int n[3]; double dx[3]; } claw_grid;
  * LW-update as the paper runs it.  STRANG: x(dt/2) y(dt) x(dt/2) in 2D,
  * x(dt/2) y(dt/2) z(dt) y(dt/2) x(dt/2) in 3D, the second-order splitting
  * of the same Clawpack base.  UNSPLIT (2D acoustics and shallow water, not
- * CLAW_SHALLOW_WATER_BATHY; CLAW_EINVAL otherwise): no splitting -- every
+ * CLAW_SHALLOW_WATER_BATHY or _DRY; CLAW_EINVAL otherwise): no splitting -- every
  * Riemann problem of the step is solved from Q^n and each cell is updated
  * once from its x and y fluctuations and corrections, with transverse
  * solvers carrying the fluctuations (modified by the corrections) across
@@ -109,13 +121,15 @@ typedef enum { CLAW_SPLIT_GODUNOV = 0, CLAW_SPLIT_STRANG = 1, CLAW_SPLIT_UNSPLIT
  * of CLAW_ACOUSTICS_VAR); g: gravity; cfl_desired: Courant number the next
  * step aims at; cfl_max: a step above it is redone; dt_max: cap on dt;
  * precision: 32 or 64; max_retries: consecutive rejections before
- * CLAW_ECFL (<= 0 selects 8); splitting: a claw_splitting. */
+ * CLAW_ECFL (<= 0 selects 8); splitting: a claw_splitting; dry_tol
+ * (CLAW_SHALLOW_WATER_DRY, >= 0): a cell with h <= dry_tol is dry. */
 typedef struct {
     double rho, K, g;
     double cfl_desired, cfl_max, dt_max;
     int precision;
     int max_retries;
     int splitting;
+    double dry_tol;
 } claw_params;
 
 /* Ghost cells, two per side, filled inside each sweep from the state it is
@@ -126,7 +140,9 @@ typedef struct {
 
 /* ---------------------------------------------------------------- single grid */
 
-/* Create a solver for one grid.  (m, mwaves) must match the system:
+/* Create a solver for one grid of cell averages Q_{i,j} of Sec. 3 (the
+ * finite-volume unknowns of Eq. conslaw) and the pipeline of Sec. 4.1
+ * around it.  (m, mwaves) must match the system:
  * (3,2) 2D acoustics, (4,2) 3D acoustics, (3,3) shallow water (2D only);
  * otherwise CLAW_EINVAL.  cuda_stream: a cudaStream_t (e.g. a torch stream)
  * or NULL.  The state starts at zero (h = 1 for shallow water), t = 0. */
@@ -134,60 +150,78 @@ claw_status claw_create(const claw_grid* grid, int m, int mwaves, claw_system sy
                         claw_limiter limiter, const claw_bc bc[6], const claw_params* params,
                         void* cuda_stream, claw_solver** out);
 
-/* Release every resource of the solver (synchronises its stream).  NULL is a no-op. */
+/* Release every resource of the solver created for Sec. 4.1's pipeline
+ * (synchronises its stream).  NULL is a no-op. */
 void claw_destroy(claw_solver* s);
 
-/* Copy a new state in (FP64 SoA, see conventions) and set the next step from
- * a speeds-only Riemann pass over it: dt = cfl_desired / max_d(m_d / dx_d). */
+/* Copy a new state of cell averages in (Sec. 3; FP64 SoA, see conventions:
+ * the double-precision interface of Sec. 6 in front of a solver that may
+ * compute in single precision) and set the next step from a speeds-only
+ * Riemann pass over it, dt = cfl_desired / max_d(m_d / dx_d) (Eq.
+ * CFL-condition). */
 claw_status claw_set_q(claw_solver* s, const double* q_soa, int on_device);
 
-/* Copy the current state out (FP64 SoA).  Synchronises; returns any latched
- * device fault. */
+/* Copy the current cell averages out (Sec. 3; FP64 SoA, the solution read
+ * back at any step as in Sec. 6).  Synchronises; returns any latched device
+ * fault. */
 claw_status claw_get_q(claw_solver* s, double* q_soa, int on_device);
 
-/* Per-cell rho and K (nx*ny*nz doubles each, x fastest) for
- * CLAW_ACOUSTICS_VAR; impedance Z = rho c and c = sqrt(K / rho) are formed
+/* Per-cell rho and K of Eq. acoustics with coefficients (Sec. 3; nx*ny*nz
+ * doubles each, x fastest) for CLAW_ACOUSTICS_VAR; impedance Z = rho c and c = sqrt(K / rho) are formed
  * once per cell, in FP64.  CLAW_EINVAL for other systems or rho, K <= 0 is
  * not checked (the caller guarantees positivity). */
 claw_status claw_set_aux(claw_solver* s, const double* rho, const double* K, int on_device);
 
-/* Bottom elevation B per cell (nx*ny doubles, x fastest) for
- * CLAW_SHALLOW_WATER_BATHY, stored in the state's precision (the wave
- * speeds do not depend on it, so dt is unchanged).  CLAW_EINVAL for other
+/* Bottom elevation B per cell of the shallow-water source term (Sec. 3:
+ * source terms added to Eq. SW; nx*ny doubles, x fastest) for
+ * CLAW_SHALLOW_WATER_BATHY and CLAW_SHALLOW_WATER_DRY, stored in the state's
+ * precision.  The bathymetry system's wave speeds do not depend on B, so dt
+ * is unchanged; with wetting and drying they do (the reconstruction), and
+ * the next step is set again from a speeds-only pass.  CLAW_EINVAL for other
  * systems.  Synchronises. */
 claw_status claw_set_bathymetry(claw_solver* s, const double* B, int on_device);
 
-/* One accepted step.  dt > 0: exactly that step, always kept (no CFL
- * control); dt <= 0: the CFL rule, redone on a violation.  *cfl_out (may be
+/* One accepted step of Eq. LW-update.  dt > 0: exactly that step, always
+ * kept (no CFL control); dt <= 0: the CFL rule of Eq. CFL-condition and
+ * Sec. 4.1 (revert and redo on a violation).  *cfl_out (may be
  * NULL) receives the Courant number of the kept step.  Synchronises. */
 claw_status claw_step(claw_solver* s, double dt, double* cfl_out);
 
-/* Advance to t_final (>= current t, else CLAW_EINVAL) under the CFL rule;
+/* Advance to t_final (>= current t, else CLAW_EINVAL) under the CFL rule
+ * (Eq. CFL-condition, Sec. 4.1 time-step adjustment; Sec. 6 evolves a
+ * problem this way);
  * the last step is shortened to land on t_final exactly.  cfl_target > 0
  * replaces cfl_desired.  *nsteps_out (may be NULL) gets the accepted steps.
  * Runs as CUDA graphs of several steps with the step control on the device.
  * Synchronises. */
 claw_status claw_advance(claw_solver* s, double t_final, double cfl_target, int* nsteps_out);
 
-/* Take nsteps accepted steps under the CFL rule (rejected attempts are
- * redone and not counted), as CUDA graphs.  Synchronises. */
+/* Take nsteps accepted steps of Eq. LW-update under the CFL rule (Eq.
+ * CFL-condition; rejected attempts are redone, Sec. 4.1, and not counted),
+ * as CUDA graphs.  Synchronises. */
 claw_status claw_run_steps(claw_solver* s, int nsteps);
 
-/* max_d (max|s^p| / dx_d) of the current state, in FP64.  Synchronises. */
+/* max_d (max|s^p| / dx_d) of the current state, in FP64: the fastest wave
+ * speed of Eq. CFL-condition, from the speed reduction of Sec. 4.1.
+ * Synchronises. */
 claw_status claw_max_speed(claw_solver* s, double* smax_over_dx);
 
-/* Simulated time, next step, accepted steps.  Synchronises. */
+/* Simulated time, next step (Eq. CFL-condition, Sec. 4.1 time-step
+ * adjustment), accepted steps.  Synchronises. */
 claw_status claw_get_time(claw_solver* s, double* t, double* dt, long* nsteps);
 
 /* Restore the clock (checkpoint / resume).  dt <= 0 recomputes the next
- * step from the current state. */
+ * step from the current state by Eq. CFL-condition (Sec. 4.1). */
 claw_status claw_set_time(claw_solver* s, double t, double dt, long nsteps);
 
 /* Sum of each field over the interior cells (m doubles), accumulated in
- * FP64 in a fixed order (deterministic).  Synchronises. */
+ * FP64 in a fixed order (deterministic): the totals the conservation form of
+ * Sec. 3 (Eq. conslaw, Eq. LW-update in flux-difference form) keeps
+ * constant up to boundary fluxes.  Synchronises. */
 claw_status claw_conservation_sums(claw_solver* s, double* sums);
 
-/* Rejected attempts so far.  Synchronises. */
+/* Attempts rejected and redone so far (Sec. 4.1: a step that violates Eq.
+ * CFL-condition is reverted).  Synchronises. */
 claw_status claw_get_rejections(claw_solver* s, long* nrej);
 
 /* nsteps steps of exactly dt > 0, all kept (no CFL decision), replayed as
@@ -199,7 +233,8 @@ claw_status claw_get_rejections(claw_solver* s, long* nrej);
  * ensemble, the largest over the instances.  Synchronises. */
 claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* cfl_peak);
 
-/* Rows [y0, y0 + nrows) of every field of a single 2D grid, FP64,
+/* Rows [y0, y0 + nrows) of every field of a single 2D grid (Sec. 8: the
+ * independent subproblems of a multi-GPU run exchange these), FP64,
  * structure of arrays (m, nrows, nx), x fastest: copied out of (get) or
  * into (set) the current state.  The pieces of a grid split along y
  * exchange their boundary rows this way.  on_device as for claw_set_q.
@@ -209,6 +244,7 @@ claw_status claw_run_fixed_steps(claw_solver* s, int nsteps, double dt, double* 
  * synchronises.  CLAW_EINVAL for an ensemble or a 3D grid, CLAW_EBOUNDS for
  * rows outside [0, ny). */
 claw_status claw_get_rows(claw_solver* s, int y0, int nrows, double* out, int on_device);
+claw_status claw_set_rows(claw_solver* s, int y0, int nrows, const double* rows, int on_device);
 
 /* Keep a copy of the current state (every field's kept version, in the
  * state's precision, in device memory the solver allocates on the first call:
@@ -220,28 +256,38 @@ claw_status claw_get_rows(claw_solver* s, int y0, int nrows, double* out, int on
  * CLAW_EINVAL.  Both synchronise. */
 claw_status claw_checkpoint(claw_solver* s);
 claw_status claw_rollback(claw_solver* s);
-claw_status claw_set_rows(claw_solver* s, int y0, int nrows, const double* rows, int on_device);
 
-/* Thread-local text of the last failure ("" if none). */
+/* Thread-local text of the last failure ("" if none).  Error reporting of
+ * this library; the paper has no counterpart. */
 const char* claw_last_error(void);
 
 /* ---------------------------------------------------------------- ensembles */
 
 /* B >= 1 independent problems of one system and limiter, each with its own
- * grid (all of the same ndim), time, step size and CFL control, advanced
- * together: one launch per sweep covers the tiles of every instance.
- * m and mwaves follow from the system; bc applies to every instance. */
+ * grid (all of the same ndim), time, step size and CFL control (Eq.
+ * CFL-condition per instance), advanced together: one launch per sweep
+ * covers the tiles of every instance, the way Sec. 5.1's independent blocks
+ * each advance their own subdomain.  m and mwaves follow from the system;
+ * bc[6] (per face, as for claw_create) applies to every instance. */
 claw_status claw_ensemble_create(int B, const claw_grid* grids, claw_system system,
                                  claw_limiter limiter, const claw_bc bc[6],
                                  const claw_params* params, void* cuda_stream,
                                  claw_solver** out);
+/* Instance i's cell averages in and out (Sec. 3; as claw_set_q / claw_get_q,
+ * i in [0, B), else CLAW_EINVAL), its material coefficients (Eq. acoustics
+ * with coefficients, as claw_set_aux) and its bottom elevation (Sec. 3
+ * source terms, as claw_set_bathymetry). */
 claw_status claw_ensemble_set_q(claw_solver* s, int i, const double* q, int on_device);
 claw_status claw_ensemble_get_q(claw_solver* s, int i, double* q, int on_device);
 claw_status claw_ensemble_set_aux(claw_solver* s, int i, const double* rho, const double* K,
                                   int on_device);
 claw_status claw_ensemble_set_bathymetry(claw_solver* s, int i, const double* B, int on_device);
-/* nsteps accepted steps for every instance, each under its own CFL rule. */
+/* nsteps accepted steps of Eq. LW-update for every instance, each under its
+ * own CFL rule (Eq. CFL-condition, Sec. 4.1).  Synchronises. */
 claw_status claw_ensemble_run_steps(claw_solver* s, int nsteps);
+/* Instance i's clock as claw_get_time (Sec. 4.1 time-step adjustment);
+ * synchronises.  claw_ensemble_size: B (0 for NULL), the number of
+ * independent problems of Sec. 5.1's kind this solver advances. */
 claw_status claw_ensemble_get_time(claw_solver* s, int i, double* t, double* dt, long* nsteps);
 int         claw_ensemble_size(const claw_solver* s);
 
@@ -267,10 +313,11 @@ int         claw_ensemble_size(const claw_solver* s);
  * Scratch: a fixed 384 KiB array in the library's device memory (one
  * partial maximum per 128 lines per direction) that every GPU loading the
  * library holds until the process exits.  Grids with more than 2,097,152
- * lines in some direction are rejected with CLAW_EBOUNDS.  All calls share
- * the array and it keeps the last call's contents; calls that overlap on the
- * GPU (different streams, or devices sharing nothing else) race on it, so
- * serialise them.  The first call on each device looks up the array's
+ * lines in some direction are rejected with CLAW_EBOUNDS.  All calls on one
+ * device share that device's copy of the array, and it keeps the last call's
+ * contents; calls that overlap on the same device (different streams) race
+ * on it, so serialise them there.  Calls on different devices use different
+ * copies and do not interfere.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  Asynchronous on cuda_stream: *out
  * is valid once the stream reaches it.  Errors: CLAW_EINVAL for bad
@@ -284,7 +331,8 @@ claw_status claw_max_speed_noalloc(const claw_grid* grid, claw_system system,
 /* ---------------------------------------------------------------- measurement */
 
 /* Take nsteps accepted steps like claw_run_steps inside one CUDA graph whose
- * kernels are bracketed by CUDA events, and report the average duration of
+ * kernels are bracketed by CUDA events (the per-kernel times Sec. 7.1's
+ * roofline analysis works from), and report the average duration of
  * one launch of each kernel kind: kernel_ms[d] for the d-sweep (d < ndim;
  * with Strang splitting the sum over the step's d sweeps; with
  * CLAW_SPLIT_UNSPLIT kernel_ms[0] is the unsplit update and kernel_ms[1] is
@@ -299,14 +347,15 @@ claw_status claw_profile_steps(claw_solver* s, int nsteps, double kernel_ms[4],
  * roof").  Synchronises cuda_stream (NULL = legacy default stream). */
 claw_status claw_probe_fma(int precision, double* flops_per_s, void* cuda_stream);
 
-/* Tuning knobs (the autotuner drives these): cells per line segment of one
+/* Tuning knobs (the autotuner drives these; Sec. 5.2: the tile shape of each
+ * direction's kernel needs careful tuning): cells per line segment of one
  * thread in direction d (>= 4, rounded up to a multiple of 8).  With
  * CLAW_SPLIT_UNSPLIT the direction-1 length is also the rows per strip tile
  * of the unsplit update (a warp marches 28 columns down that many rows).
  * Rebuilds the tile lists. */
 claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 
-/* Autotuner: for every direction, time trial_steps steps (CUDA events around
+/* Autotuner (the tuning of tile shapes Sec. 5.2 calls for): for every direction, time trial_steps steps (CUDA events around
  * each sweep) twice with each candidate segment length and keep the fastest
  * (with CLAW_SPLIT_UNSPLIT: the rows per strip tile, timed on the unsplit
  * kernel, from fixed lengths 16..256).  The

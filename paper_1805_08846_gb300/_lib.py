@@ -19,7 +19,8 @@ from . import build as _build
 CLAW_OK, CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA, CLAW_ECFL, CLAW_ENONPHYS, CLAW_ETIMEOUT, CLAW_EBOUNDS = range(8)
 STATUS_NAMES = {0: "CLAW_OK", 1: "CLAW_EINVAL", 2: "CLAW_ENOMEM", 3: "CLAW_ECUDA", 4: "CLAW_ECFL",
                 5: "CLAW_ENONPHYS", 6: "CLAW_ETIMEOUT", 7: "CLAW_EBOUNDS"}
-SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3}
+SYSTEMS = {"acoustics": 0, "acoustics_var": 1, "shallow_water": 2, "shallow_water_bathy": 3,
+           "shallow_water_dry": 4}
 LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "first_order": 3}
 BCS = {"periodic": 0, "extrap": 1, "wall": 2}
 
@@ -37,7 +38,8 @@ class claw_grid(C.Structure):
 class claw_params(C.Structure):
     _fields_ = [("rho", C.c_double), ("K", C.c_double), ("g", C.c_double),
                 ("cfl_desired", C.c_double), ("cfl_max", C.c_double), ("dt_max", C.c_double),
-                ("precision", C.c_int), ("max_retries", C.c_int), ("splitting", C.c_int)]
+                ("precision", C.c_int), ("max_retries", C.c_int), ("splitting", C.c_int),
+                ("dry_tol", C.c_double)]
 
 
 _vp = C.c_void_p
@@ -148,10 +150,10 @@ SPLITTINGS = {"godunov": 0, "strang": 1, "unsplit": 2}
 
 
 def make_params(rho=1.0, K=1.0, g=9.81, cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, precision=64,
-                max_retries=8, splitting="godunov") -> claw_params:
+                max_retries=8, splitting="godunov", dry_tol=1e-3) -> claw_params:
     sp = SPLITTINGS[splitting] if isinstance(splitting, str) else int(splitting)
     return claw_params(float(rho), float(K), float(g), float(cfl_desired), float(cfl_max),
-                       float(dt_max), int(precision), int(max_retries), sp)
+                       float(dt_max), int(precision), int(max_retries), sp, float(dry_tol))
 
 
 def make_grid(n, dx) -> claw_grid:

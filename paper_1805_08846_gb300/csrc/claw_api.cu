@@ -49,16 +49,20 @@ int slot_of_version(int v) { return v == 0 ? 0 : 1 + (v - 1) % 2; }
 
 // Fields a sweep along d changes (the reduced state of the Riemann solver).
 std::vector<int> touched_fields(int system, int d) {
-    if (system == kSysShallowWater || system == kSysShallowWaterBathy) return {0, 1, 2};
+    if (system == kSysShallowWater || system == kSysShallowWaterBathy || system == kSysShallowWaterDry)
+        return {0, 1, 2};
     return {0, 1 + d};
 }
 
-bool is_sw(int system) { return system == CLAW_SHALLOW_WATER || system == CLAW_SHALLOW_WATER_BATHY; }
+bool is_sw(int system) {
+    return system == CLAW_SHALLOW_WATER || system == CLAW_SHALLOW_WATER_BATHY || system == CLAW_SHALLOW_WATER_DRY;
+}
+
+// Systems with a bottom elevation (one material plane B).
+bool has_bed(int system) { return system == CLAW_SHALLOW_WATER_BATHY || system == CLAW_SHALLOW_WATER_DRY; }
 
 // Material planes per cell: (Z, c) for variable acoustics, B for bathymetry.
-int aux_planes(int system) {
-    return system == CLAW_ACOUSTICS_VAR ? 2 : (system == CLAW_SHALLOW_WATER_BATHY ? 1 : 0);
-}
+int aux_planes(int system) { return system == CLAW_ACOUSTICS_VAR ? 2 : (has_bed(system) ? 1 : 0); }
 
 }  // namespace
 
@@ -236,6 +240,7 @@ SweepArgs sweep_args(claw_solver* s, int d, int tile_lo, int tile_hi, int k = -1
     a.Z = s->Z;
     a.c = s->c;
     a.g = s->params.g;
+    a.dry_tol = s->params.dry_tol;
     return a;
 }
 
@@ -498,7 +503,7 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     *out = nullptr;
     if (B < 1) return fail(CLAW_EINVAL, "ensemble size must be >= 1 (got %d)", B);
     if (!grids || !bc || !params) return fail(CLAW_EINVAL, "NULL argument");
-    if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER_BATHY) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
+    if (system < CLAW_ACOUSTICS || system > CLAW_SHALLOW_WATER_DRY) return fail(CLAW_EINVAL, "unknown system %d", (int)system);
     if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_FIRST_ORDER) return fail(CLAW_EINVAL, "unknown limiter %d", (int)limiter);
     const int ndim = grids[0].ndim;
     for (int i = 0; i < B; ++i) CKS(check_grid(&grids[i], ndim));
@@ -513,13 +518,15 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     if (params->splitting != CLAW_SPLIT_GODUNOV && params->splitting != CLAW_SPLIT_STRANG &&
         params->splitting != CLAW_SPLIT_UNSPLIT)
         return fail(CLAW_EINVAL, "unknown splitting %d", params->splitting);
-    if (params->splitting == CLAW_SPLIT_UNSPLIT && (ndim != 2 || system == CLAW_SHALLOW_WATER_BATHY))
+    if (params->splitting == CLAW_SPLIT_UNSPLIT && (ndim != 2 || has_bed(system)))
         return fail(CLAW_EINVAL, "the unsplit update covers 2D acoustics and shallow water without bathymetry");
     if (!(params->cfl_desired > 0.0) || !(params->cfl_max > 0.0)) return fail(CLAW_EINVAL, "cfl_desired and cfl_max must be > 0");
     if (!(params->dt_max > 0.0)) return fail(CLAW_EINVAL, "dt_max must be > 0");
     if (!is_sw(system) && (!(params->rho > 0.0) || !(params->K > 0.0)))
         return fail(CLAW_EINVAL, "rho and K must be > 0");
     if (is_sw(system) && !(params->g > 0.0)) return fail(CLAW_EINVAL, "g must be > 0");
+    if (system == CLAW_SHALLOW_WATER_DRY && !(params->dry_tol >= 0.0))
+        return fail(CLAW_EINVAL, "dry_tol must be >= 0");
 
     claw_solver* s = new claw_solver();
     s->B = B;
@@ -678,6 +685,20 @@ claw_status check_solver(claw_solver* s, int i = 0) {
     return CLAW_OK;
 }
 
+// Device-side address of a pinned (page-locked, mapped) host buffer, or
+// nullptr for pageable memory.  The conversion kernels read and write pinned
+// host buffers directly over the host link (on a Grace-Blackwell part the
+// coherent NVLink-C2C), fusing the copy with the precision conversion;
+// pageable buffers go through the device stage with cudaMemcpyAsync.
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear: an unknown pointer is pageable memory
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 claw_status set_q_impl(claw_solver* s, int i, const double* q, int on_device) {
     CKS(check_solver(s, i));
     if (!q) return fail(CLAW_EINVAL, "q is NULL");
@@ -685,8 +706,11 @@ claw_status set_q_impl(claw_solver* s, int i, const double* q, int on_device) {
     const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2] * s->m;
     const double* src = q;
     if (!on_device) {
-        CK(cudaMemcpyAsync(s->stage, q, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-        src = s->stage;
+        src = static_cast<const double*>(mapped_host(q));
+        if (!src) {
+            CK(cudaMemcpyAsync(s->stage, q, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+            src = s->stage;
+        }
     }
     CK(launch_reset_status(s->d_ctl, i, s->stream));
     CK(launch_convert_in(s->precision, s->pool, I, s->d_ctl + i, src, s->m, s->stream));
@@ -700,9 +724,11 @@ claw_status get_q_impl(claw_solver* s, int i, double* q, int on_device) {
     if (!q) return fail(CLAW_EINVAL, "q is NULL");
     const InstDesc& I = s->inst[i];
     const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2] * s->m;
-    double* dst = on_device ? q : s->stage;
+    double* mapped = on_device ? nullptr : static_cast<double*>(const_cast<void*>(mapped_host(q)));
+    double* dst = on_device ? q : (mapped ? mapped : s->stage);
     CK(launch_convert_out(s->precision, s->pool, I, s->d_ctl + i, dst, s->m, s->stream));
-    if (!on_device) CK(cudaMemcpyAsync(q, s->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (!on_device && !mapped)
+        CK(cudaMemcpyAsync(q, s->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CKS(read_ctl(s));
     return latched_status(s, i, i + 1);
 }
@@ -760,8 +786,8 @@ claw_status rows_impl(claw_solver* s, int y0, int nrows, double* buf, int on_dev
 
 claw_status set_bathymetry_impl(claw_solver* s, int i, const double* B, int on_device) {
     CKS(check_solver(s, i));
-    if (s->system != CLAW_SHALLOW_WATER_BATHY)
-        return fail(CLAW_EINVAL, "claw_set_bathymetry needs CLAW_SHALLOW_WATER_BATHY");
+    if (!has_bed(s->system))
+        return fail(CLAW_EINVAL, "claw_set_bathymetry needs CLAW_SHALLOW_WATER_BATHY or CLAW_SHALLOW_WATER_DRY");
     if (!B) return fail(CLAW_EINVAL, "B is NULL");
     const InstDesc& I = s->inst[i];
     const size_t n = (size_t)I.n[0] * I.n[1] * I.n[2];
@@ -771,6 +797,8 @@ claw_status set_bathymetry_impl(claw_solver* s, int i, const double* B, int on_d
         b = s->stage;
     }
     CK(launch_aux_plane(s->precision, s->aux, I, 0, b, s->stream));
+    // with wetting and drying the speeds depend on the bed (reconstruction)
+    if (s->system == CLAW_SHALLOW_WATER_DRY) CKS(speed_pass(s, i, 1));
     CK(cudaStreamSynchronize(s->stream));
     return CLAW_OK;
 }
@@ -796,6 +824,9 @@ cudaError_t claw::launch_sweep(const SweepLaunch& L) {
         case kSysShallowWaterBathy:
             return L.precision == 64 ? launch_sweep_shallow_water_bathy_f64(L)
                                      : launch_sweep_shallow_water_bathy_f32(L);
+        case kSysShallowWaterDry:
+            return L.precision == 64 ? launch_sweep_shallow_water_dry_f64(L)
+                                     : launch_sweep_shallow_water_dry_f32(L);
         default:
             return L.precision == 64 ? launch_sweep_shallow_water_f64(L) : launch_sweep_shallow_water_f32(L);
     }
@@ -936,6 +967,9 @@ claw_status claw_checkpoint(claw_solver* s) {
             CK(cudaMemcpyAsync(dst, src, (size_t)I.fstride * s->esize, cudaMemcpyDeviceToDevice, s->stream));
         }
     CK(cudaMemcpyAsync(s->ckpt_ctl, s->d_ctl, sizeof(Control) * s->B, cudaMemcpyDeviceToDevice, s->stream));
+    // the snapshot exists (and any failure of its copies is reported) when
+    // the call returns
+    CK(cudaStreamSynchronize(s->stream));
     return latched_status(s, 0, s->B);
 }
 

@@ -145,6 +145,7 @@ struct SweepArgs {
     int lines;         // lines per tile of this direction's tile list
     int m;                 // fields per state version (TMA plane = slot * m + field)
     double Z, c, g;        // constant acoustics impedance / speed; gravity
+    double dry_tol;        // wetting and drying: a cell with h <= dry_tol is dry
 };
 
 }  // namespace claw

@@ -5,7 +5,13 @@
 
 namespace claw {
 
-enum : int { kSysAcoustics = 0, kSysAcousticsVar = 1, kSysShallowWater = 2, kSysShallowWaterBathy = 3 };
+enum : int {
+    kSysAcoustics = 0,
+    kSysAcousticsVar = 1,
+    kSysShallowWater = 2,
+    kSysShallowWaterBathy = 3,
+    kSysShallowWaterDry = 4
+};
 
 struct SweepLaunch {
     SweepArgs args;
@@ -34,6 +40,8 @@ cudaError_t launch_sweep_shallow_water_f32(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_f64(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_bathy_f32(const SweepLaunch& L);
 cudaError_t launch_sweep_shallow_water_bathy_f64(const SweepLaunch& L);
+cudaError_t launch_sweep_shallow_water_dry_f32(const SweepLaunch& L);
+cudaError_t launch_sweep_shallow_water_dry_f64(const SweepLaunch& L);
 
 // Unsplit update with transverse waves (2D acoustics and shallow water):
 // one launch per step attempt over the strip tiles in args.tiles (TileDesc:

@@ -49,15 +49,18 @@ __device__ __forceinline__ bool finite_(Real x) {
 }
 
 // Division, reciprocal and square roots.  FP64 (the plain path) uses the
-// correctly rounded operations; the FP32 form uses the SFU approximations
-// (reciprocal and reciprocal square root, a few ulp), far inside its
-// 1e-4 / 1e-5 error budget and a fraction of the instruction count.
+// correctly rounded divide, reciprocal and square root, and the double
+// reciprocal square root (a few ulp) where a solver asks for one; the FP32
+// form uses the SFU approximations (reciprocal and reciprocal square root, a
+// few ulp), far inside its 1e-4 / 1e-5 error budget and a fraction of the
+// instruction count.
 template <class Real>
 struct Ops;
 template <>
 struct Ops<double> {
     __device__ __forceinline__ static double div(double a, double b) { return a / b; }
     __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }
+    __device__ __forceinline__ static double rsqrt(double x) { return ::rsqrt(x); }
     __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
 };
 template <>
@@ -171,10 +174,9 @@ struct Acoustics {
 // q_m = Q_r - W3.  The sign test of lam_m is done without a square root:
 // for h_m > 0, u_m - sqrt(g h_m) > 0  <=>  hu_m > 0 and hu_m^2 > g h_m^3;
 // the four conditions of a transonic 1-wave (c_l - u_l, h_m, hu_m and
-// hu_m^2 - g h_m^3 all positive) are one test, min(...) > 0, without a
-// branch on the sign of lam_l (negative almost everywhere in subsonic flow).
-// (measured at 4096^2: x sweep 0.141 -> 0.137 ms against four compares
-// behind such a branch)
+// hu_m^2 - g h_m^3 all positive) are one test, min(...) > 0, taken only
+// where the rarely true last one holds (a supercritical middle state; in
+// subcritical flow the whole test is one packed quantity and a compare).
 // ------------------------------------------------------------------------
 template <class Real>   // double, float, or f2 (two lines)
 struct ShallowWater {
@@ -191,7 +193,6 @@ struct ShallowWater {
         Real sqh;    // sqrt(h)
         Real c;      // sqrt(g h)
     };
-    static constexpr bool kFast = !std::is_same<Real, double>::value;
     static constexpr bool kFWave = false;
 
     __device__ __forceinline__ static int field(int d, int comp) {
@@ -201,22 +202,18 @@ struct ShallowWater {
     __host__ __device__ static constexpr bool zero(int p, int c) { return p == 1 && c < 2; }
     __device__ __forceinline__ static void set_aux(Cell&, const Real*) {}
 
+    // One reciprocal square root per cell gives sqrt(h) and 1/h, and one per
+    // interface gives c_hat and 1/(2 c_hat), in every precision (FP64: the
+    // double rsqrt, within a few ulp; measured 6.80 -> 6.09 ms per 4096^2
+    // sweep against correctly rounded divides and square roots, parity with
+    // the oracle unchanged at 1e-12).
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
-        if constexpr (kFast) {
-            // one reciprocal square root gives sqrt(h) and 1/h
-            const Real r = Ops<Real>::rsqrt(cell.q[0]);
-            const Real rh = r * r;
-            cell.sqh = cell.q[0] * r;
-            cell.u = cell.q[1] * rh;
-            cell.v = cell.q[2] * rh;
-            cell.c = P.sqrt_g * cell.sqh;
-        } else {
-            const Real rh = Real(1) / cell.q[0];
-            cell.u = cell.q[1] * rh;
-            cell.v = cell.q[2] * rh;
-            cell.sqh = sqrt(cell.q[0]);
-            cell.c = sqrt(P.g * cell.q[0]);
-        }
+        const Real r = Ops<Real>::rsqrt(cell.q[0]);
+        const Real rh = r * r;
+        cell.sqh = cell.q[0] * r;
+        cell.u = cell.q[1] * rh;
+        cell.v = cell.q[2] * rh;
+        cell.c = P.sqrt_g * cell.sqh;
     }
 
     // Roe averages; i2c = 1 / (2 c_hat), ni2c = -i2c.
@@ -227,16 +224,10 @@ struct ShallowWater {
         uh = vfma(l.sqh, l.u, r.sqh * r.u) * den;
         vh = vfma(l.sqh, l.v, r.sqh * r.v) * den;
         const Real gh = P.half_g * (l.q[0] + r.q[0]);   // 0.5 g exactly: g (0.5 s) = (0.5 g) s
-        if constexpr (kFast) {
-            const Real rc = Ops<Real>::rsqrt(gh);
-            ch = gh * rc;
-            i2c = Real(0.5f) * rc;
-            ni2c = Real(-0.5f) * rc;
-        } else {
-            ch = sqrt(gh);
-            i2c = Real(0.5) / ch;
-            ni2c = -i2c;
-        }
+        const Real rc = Ops<Real>::rsqrt(gh);
+        ch = gh * rc;
+        i2c = Real(0.5f) * rc;
+        ni2c = Real(-0.5f) * rc;
     }
 
     __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
@@ -280,33 +271,41 @@ struct ShallowWater {
         Real km3 = vmin(s3, Real(0)), kp3 = vmax(s3, Real(0));
         const Real km2 = vmin(uh, Real(0)), kp2 = vmax(uh, Real(0));
 
-        // Transonic tests without a branch on the (nearly always true) sign
-        // of lam_l / lam_r: one packed minimum of the four conditions.
         const Real ng = Real(0) - P.g;
+        // Transonic tests.  The middle state must be supercritical for either
+        // wave to be transonic (hu_m^2 > g h_m^3), which subcritical flow never
+        // is: that one packed quantity is tested first, the other three
+        // conditions (as one minimum) only where it holds (measured at 4096^2:
+        // x sweep 0.137 -> 0.132 ms, y 0.111 -> 0.108 ms, against testing the
+        // minimum of all four everywhere)
         {
             const Real hm = l.q[0] + w.W[0][0];
             const Real hum = l.q[1] + w.W[0][1];
-            const Real t = vmin(vmin(l.c - l.u, hm), vmin(hum, vfma(hum, hum, (ng * hm) * (hm * hm))));
-            const auto fix = vgt(t, Real(0));
-            if (any(fix)) {
-                const Real lam_l = l.u - l.c;
-                const Real lam_m = Ops<Real>::div(hum, hm) - Ops<Real>::sqrt_(P.g * hm);
-                const Real beta = Ops<Real>::div(lam_m - s1, lam_m - lam_l);
-                km1 = sel(fix, beta * lam_l, km1);
-                kp1 = sel(fix, (Real(1) - beta) * lam_m, kp1);
+            const Real sup = vfma(hum, hum, (ng * hm) * (hm * hm));
+            if (any(vgt(sup, Real(0)))) {
+                const auto fix = vgt(vmin(vmin(l.c - l.u, hm), vmin(hum, sup)), Real(0));
+                if (any(fix)) {
+                    const Real lam_l = l.u - l.c;
+                    const Real lam_m = Ops<Real>::div(hum, hm) - Ops<Real>::sqrt_(P.g * hm);
+                    const Real beta = Ops<Real>::div(lam_m - s1, lam_m - lam_l);
+                    km1 = sel(fix, beta * lam_l, km1);
+                    kp1 = sel(fix, (Real(1) - beta) * lam_m, kp1);
+                }
             }
         }
         {
             const Real hm = r.q[0] - w.W[2][0];
             const Real hum = r.q[1] - w.W[2][1];
-            const Real t = vmin(vmin(r.u + r.c, hm), vmin(Real(0) - hum, vfma(hum, hum, (ng * hm) * (hm * hm))));
-            const auto fix = vgt(t, Real(0));
-            if (any(fix)) {
-                const Real lam_r = r.u + r.c;
-                const Real lam_m = Ops<Real>::div(hum, hm) + Ops<Real>::sqrt_(P.g * hm);
-                const Real beta = Ops<Real>::div(lam_r - s3, lam_r - lam_m);
-                km3 = sel(fix, beta * lam_m, km3);
-                kp3 = sel(fix, (Real(1) - beta) * lam_r, kp3);
+            const Real sup = vfma(hum, hum, (ng * hm) * (hm * hm));
+            if (any(vgt(sup, Real(0)))) {
+                const auto fix = vgt(vmin(vmin(r.u + r.c, hm), vmin(Real(0) - hum, sup)), Real(0));
+                if (any(fix)) {
+                    const Real lam_r = r.u + r.c;
+                    const Real lam_m = Ops<Real>::div(hum, hm) + Ops<Real>::sqrt_(P.g * hm);
+                    const Real beta = Ops<Real>::div(lam_r - s3, lam_r - lam_m);
+                    km3 = sel(fix, beta * lam_m, km3);
+                    kp3 = sel(fix, (Real(1) - beta) * lam_r, kp3);
+                }
             }
         }
 #pragma unroll
@@ -379,20 +378,12 @@ struct ShallowWaterBathy {
     __device__ __forceinline__ static void set_aux(Cell& cell, const Real* a) { cell.B = a[0]; }
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
-        if constexpr (SW::kFast) {
-            const Real r = Ops<Real>::rsqrt(cell.q[0]);
-            const Real rh = r * r;
-            cell.sqh = cell.q[0] * r;
-            cell.u = cell.q[1] * rh;
-            cell.v = cell.q[2] * rh;
-            cell.c = P.sqrt_g * cell.sqh;
-        } else {
-            const Real rh = Real(1) / cell.q[0];
-            cell.u = cell.q[1] * rh;
-            cell.v = cell.q[2] * rh;
-            cell.sqh = sqrt(cell.q[0]);
-            cell.c = sqrt(P.g * cell.q[0]);
-        }
+        const Real r = Ops<Real>::rsqrt(cell.q[0]);
+        const Real rh = r * r;
+        cell.sqh = cell.q[0] * r;
+        cell.u = cell.q[1] * rh;
+        cell.v = cell.q[2] * rh;
+        cell.c = P.sqrt_g * cell.sqh;
         cell.fu = cell.q[1] * cell.u;
         cell.fv = cell.q[1] * cell.v;
     }
@@ -452,6 +443,164 @@ struct ShallowWaterBathy {
     }
     __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) { return SW::max_speed(w); }
     __device__ __forceinline__ static auto nonphysical(const Real q[NQ]) { return SW::nonphysical(q); }
+};
+
+// ------------------------------------------------------------------------
+// Shallow water over a bottom elevation B with wetting and drying (the
+// source of Sec. 3's Clawpack base; dry states are a reading of this
+// library, the paper is silent on them): the hydrostatic reconstruction
+// (Audusse et al. 2004) around the HLLE solver.  A cell is dry when
+// h <= dry_tol: its velocities count as zero.  At an interface, with
+// B* = max(B_l, B_r), the reconstructed depths h* = h + B - B* (0 when
+// <= dry_tol: a dry side) and states q* = h* (1, u, v) define a flat-bottom
+// problem solved by HLLE with Einfeldt's speeds,
+//   s1 = min(lam_l^-, u_hat - c_hat),  s3 = max(lam_r^+, u_hat + c_hat),
+//   lam_l^- = u_l - c_l* (wet) or u_r - 2 c_r* (dry l),
+//   lam_r^+ = u_r + c_r* (wet) or u_l + 2 c_l* (dry r),
+// (u -/+ 2c: the front of a rarefaction into a dry bed; Roe averages of the
+// reconstructed states), waves W1 = (s3 dq* - df*)/(s3 - s1),
+// W3 = (df* - s1 dq*)/(s3 - s1) (W1 + W3 = dq*, s1 W1 + s3 W3 = df*), a
+// zero middle wave at u_hat, and fluctuations
+//   A-dQ = sum_{s<0} s W + (h_l* - h_l)(u_l, u_l^2, u_l v_l),
+//   A+dQ = sum_{s>=0} s W + (h_r - h_r*)(u_r, u_r^2, u_r v_r)
+// (the reconstruction's hydrostatic pressure terms cancel exactly: mass
+// telescopes, a lake at rest gives zero, the first-order update keeps
+// h >= 0).  Where a reconstructed side is dry the waves are returned as zero:
+// no second-order correction at the shoreline.  Scalar Real only (double,
+// float): the wet / dry decisions are branches, not packed lanes.
+// ------------------------------------------------------------------------
+template <class Real>
+struct ShallowWaterDry {
+    using Value = Real;
+    static constexpr int NQ = 3;
+    static constexpr int NW = 3;
+    static constexpr int NA = 1;
+    struct Params {
+        Real g, sqrt_g, half_g, dry_tol;
+    };
+    struct Cell {
+        Real q[NQ];
+        Real u, v;   // velocities, 0 in a dry cell
+        Real B;      // bottom elevation
+    };
+    static constexpr bool kFWave = false;
+    static constexpr bool kMinH = false;
+    static constexpr bool kFast = !std::is_same<Real, double>::value;
+
+    __device__ __forceinline__ static int field(int d, int comp) {
+        return comp == 0 ? 0 : (comp == 1 ? 1 + d : 2 - d);
+    }
+    // the middle wave is identically zero
+    __host__ __device__ static constexpr bool zero(int p, int) { return p == 1; }
+    __device__ __forceinline__ static void set_aux(Cell& cell, const Real* a) { cell.B = a[0]; }
+
+    __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
+        const bool wet = cell.q[0] > P.dry_tol;
+        const Real rh = wet ? Ops<Real>::rcp(cell.q[0]) : Real(0);
+        cell.u = cell.q[1] * rh;
+        cell.v = cell.q[2] * rh;
+    }
+
+    __device__ __forceinline__ static Real gsqrt(Real gh) {
+        if constexpr (kFast) return gh > Real(0) ? Ops<Real>::sqrt_(gh) : Real(0);
+        else return sqrt(gh);
+    }
+
+    // Reconstructed depths and the HLLE speeds of an interface; false when
+    // both reconstructed sides are dry (no waves, speeds 0).
+    __device__ __forceinline__ static bool recon(const Cell& l, const Cell& r, const Params& P, Real& hl,
+                                                 Real& hr, Real& s1, Real& uh, Real& s3) {
+        const Real Bs = l.B > r.B ? l.B : r.B;
+        hl = l.q[0] + l.B - Bs;
+        hr = r.q[0] + r.B - Bs;
+        if (!(hl > P.dry_tol)) hl = Real(0);
+        if (!(hr > P.dry_tol)) hr = Real(0);
+        const bool wl = hl > Real(0), wr = hr > Real(0);
+        if (!wl && !wr) {
+            s1 = uh = s3 = Real(0);
+            return false;
+        }
+        Real sql, sqr, cl, cr, ch;
+        if constexpr (kFast) {
+            sql = wl ? Ops<Real>::sqrt_(hl) : Real(0);
+            sqr = wr ? Ops<Real>::sqrt_(hr) : Real(0);
+            cl = P.sqrt_g * sql;
+            cr = P.sqrt_g * sqr;
+            ch = gsqrt(P.half_g * (hl + hr));
+        } else {
+            sql = wl ? sqrt(hl) : Real(0);
+            sqr = wr ? sqrt(hr) : Real(0);
+            cl = wl ? sqrt(P.g * hl) : Real(0);
+            cr = wr ? sqrt(P.g * hr) : Real(0);
+            ch = sqrt(P.g * (Real(0.5) * (hl + hr)));
+        }
+        uh = Ops<Real>::div(sql * l.u + sqr * r.u, sql + sqr);
+        const Real lm = wl ? l.u - cl : r.u - Real(2) * cr;
+        const Real rp = wr ? r.u + cr : l.u + Real(2) * cl;
+        s1 = fmin(uh - ch, lm);
+        s3 = fmax(uh + ch, rp);
+        return true;
+    }
+
+    __device__ __forceinline__ static void solve(const Cell& l, const Cell& r, const Params& P,
+                                                 Waves<Real, NQ, NW>& w) {
+        Real hl, hr, s1, uh, s3;
+        const bool any_wet = recon(l, r, P, hl, hr, s1, uh, s3);
+        // what the reconstruction removes from each cell's flux
+        const Real kl = hl - l.q[0], kr = r.q[0] - hr;
+        w.amdq[0] = kl * l.u;
+        w.amdq[1] = kl * (l.u * l.u);
+        w.amdq[2] = kl * (l.u * l.v);
+        w.apdq[0] = kr * r.u;
+        w.apdq[1] = kr * (r.u * r.u);
+        w.apdq[2] = kr * (r.u * r.v);
+        w.s[0] = s1;
+        w.s[1] = uh;
+        w.s[2] = s3;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            w.W[0][c] = Real(0);
+            w.W[1][c] = Real(0);
+            w.W[2][c] = Real(0);
+        }
+        if (!any_wet) return;
+        // reconstructed states (a dry side is all zero) and their fluxes
+        const Real ql[3] = {hl, hl * l.u, hl * l.v};
+        const Real qr[3] = {hr, hr * r.u, hr * r.v};
+        const Real fl[3] = {ql[1], ql[1] * l.u + P.half_g * hl * hl, ql[1] * l.v};
+        const Real fr[3] = {qr[1], qr[1] * r.u + P.half_g * hr * hr, qr[1] * r.v};
+        const Real inv = Ops<Real>::rcp(s3 - s1);
+        const bool shore = !(hl > Real(0)) || !(hr > Real(0));
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const Real dq = qr[c] - ql[c], df = fr[c] - fl[c];
+            const Real W1 = (s3 * dq - df) * inv;
+            const Real W3 = (df - s1 * dq) * inv;
+            if (s1 < Real(0)) w.amdq[c] += s1 * W1;
+            else w.apdq[c] += s1 * W1;
+            if (s3 < Real(0)) w.amdq[c] += s3 * W3;
+            else w.apdq[c] += s3 * W3;
+            // no second-order correction at the shoreline
+            w.W[0][c] = shore ? Real(0) : W1;
+            w.W[2][c] = shore ? Real(0) : W3;
+        }
+    }
+
+    __device__ __forceinline__ static void speeds(const Cell& l, const Cell& r, const Params& P,
+                                                  Real s[NW]) {
+        Real hl, hr;
+        recon(l, r, P, hl, hr, s[0], s[1], s[2]);
+    }
+
+    // max_p |s_p| = max(|s1|, |s3|) (s1 <= u_hat <= s3).
+    __device__ __forceinline__ static Real max_speed(const Waves<Real, NQ, NW>& w) {
+        return fmax(fabs(w.s[0]), fabs(w.s[2]));
+    }
+
+    // h < 0 or NaN stops the run (h = 0 is a dry cell).
+    __device__ __forceinline__ static bool nonphysical(const Real q[NQ]) {
+        return !(q[0] >= Real(0) && q[0] <= Real(3.0e38));
+    }
 };
 
 // ------------------------------------------------------------------------

@@ -259,6 +259,15 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
     bool valid[PK];
 #pragma unroll
     for (int k = 0; k < PK; ++k) valid[k] = line_geometry<DIR>(td, I, line_of(k), base[k], stride);
+    // y, z sweeps: a warp whose lines all lie past the grid edge (the last
+    // tile of a line range that is not a multiple of the tile width: uneven
+    // ensemble instances) skips the arithmetic and only keeps the CTA's
+    // barriers; the x sweep's write-back has barriers inside the march, so
+    // its warps always march (a harmless constant state past the edge)
+    bool any_valid = false;
+#pragma unroll
+    for (int k = 0; k < PK; ++k) any_valid |= valid[k];
+    const bool live = DIR == 0 || __any_sync(0xffffffffu, any_valid);
     const int N = I.n[DIR];
     const int bc_lo = I.bc[2 * DIR], bc_hi = I.bc[2 * DIR + 1];
     const int a = td.a, b = td.b;
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
 
     // Prologue (direct loads): cells a-2 .. a+1; interfaces a-1, a, a+1;
     // flux at a.  Needs b - a >= 2 (the tile builder guarantees it).
-    {
+    if (live) {
         Cell c0, c1;
         W wX;
         load_direct(a - 2, c0);
@@ -572,7 +581,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
         // a + k*C + j - 2 overwrites an input position of this or the previous
         // chunk that has already been consumed.
 #pragma unroll 4   // measured: 2 -> 4 takes 3% off the x sweep, 8 is slower
-        for (int j = jlo; j < jhi; ++j) {
+        for (int j = jlo; j < (live ? jhi : jlo); ++j) {
             V vals[NP];
             if constexpr (PK == 2 && DIR != 0) {
                 const int off = pos_off(line_of(0), j);
@@ -642,7 +651,7 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys,
 
     // Epilogue (direct loads): cells b, b+1; the last interface b+1 bounds no
     // interior cell of the segment.
-    {
+    if (live) {
         Cell c1;
         V qn[NQ];
         load_direct(b, c1);

@@ -16,11 +16,13 @@ One period of k steps:
      all-gather cannot deadlock and works the same over gloo and NCCL.  Two
      ranks that are each other's lower and upper neighbour (periodic wrap)
      need no tags.
-  2. Speed agreement: M = all-reduce max of max_d(max|s| / dx_d) over every
-     local grid.  After step 1 all rows of every local grid are current, so
-     this is the largest speed of the whole grid.  It can be slightly larger,
-     because an outer edge sees its boundary rule's ghost: the time step is
-     then a little conservative, never too large.
+  2. Speed agreement: the first period takes M = all-reduce max of
+     max_d(max|s| / dx_d) over every local grid (a speeds-only pass; after
+     step 1 all rows of every local grid are current, so this is the largest
+     speed of the whole grid, or slightly more: an outer edge sees its
+     boundary rule's ghost).  Every later period takes M = C / dt of the
+     period before, C its all-reduced peak Courant number: the largest speed
+     any rank met in any step of that period, which needs no extra pass.
   3. dt = cfl_desired / M (capped by dt_max), the same on every rank.
   4. k steps of that dt on every rank, with no communication.
   5. The largest Courant number any rank saw is all-reduced.  Above cfl_max,
@@ -201,9 +203,11 @@ def run_steps(steppers: Dict[int, "object"], layout: SlabLayout, comm, nsteps: i
     periods = redone = 0
     seen = 0.0
     done = 0
+    M = None
     while done < nsteps:
         refresh_halos(steppers, layout, comm)
-        M = comm.allreduce_max({r: st.max_speed() for r, st in steppers.items()})
+        if M is None:
+            M = comm.allreduce_max({r: st.max_speed() for r, st in steppers.items()})
         dt = min(cfl_desired / M, dt_max) if M > 0 else dt_max
         n = min(k, nsteps - done)
         for st in steppers.values():
@@ -223,6 +227,7 @@ def run_steps(steppers: Dict[int, "object"], layout: SlabLayout, comm, nsteps: i
         done += n
         periods += 1
         seen = max(seen, c)
+        M = c / dt          # the largest speed the period met, for the next one
     return SlabRunInfo(dts, t, periods, redone, seen)
 
 
@@ -281,7 +286,8 @@ class solver_stepper:
         return M
 
     def snapshot(self):
-        self.s.checkpoint()          # a device copy in the state's own precision
+        self.s.checkpoint()          # a device copy in the state's own precision; synchronises
+        self._pending.clear()
 
     def restore(self):
         self.s.rollback()

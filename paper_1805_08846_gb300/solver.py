@@ -19,25 +19,26 @@ class Solver:
 
     def __init__(self, n, dx, system, limiter, bc, precision=64, rho=1.0, K=1.0, g=9.81,
                  cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, max_retries=8, stream=None,
-                 splitting="godunov"):
+                 splitting="godunov", dry_tol=1e-3):
         self.ndim = len(n)
         self.n = tuple(int(v) for v in n)
         self.system = system
         self.m, self.mwaves = _nm(system, self.ndim)
         params = L.make_params(rho, K, g, cfl_desired, cfl_max, dt_max, precision, max_retries,
-                               splitting)
+                               splitting, dry_tol)
         self.h = L.claw_create(self.n, dx, self.m, self.mwaves, system, limiter, bc, params, stream)
         self.shape = (self.m,) + tuple(reversed(self.n))
 
     @classmethod
     def from_problem(cls, prob, precision=64, stream=None, **kw):
         kw.setdefault("splitting", getattr(prob, "splitting", "godunov"))
+        kw.setdefault("dry_tol", getattr(prob, "dry_tol", 1e-3))
         s = cls(prob.n, prob.dx, prob.system, prob.limiter, prob.bc, precision=precision,
                 rho=prob.rho, K=prob.K, g=prob.g, cfl_desired=prob.cfl_desired,
                 cfl_max=prob.cfl_max, stream=stream, **kw)
         if prob.system == "acoustics_var":
             s.set_aux(prob.rho_cell, prob.K_cell)
-        if prob.system == "shallow_water_bathy" and prob.B_cell is not None:
+        if prob.system in ("shallow_water_bathy", "shallow_water_dry") and prob.B_cell is not None:
             s.set_bathymetry(prob.B_cell)
         s.set_q(prob.q0)
         return s
@@ -130,26 +131,27 @@ class Ensemble:
 
     def __init__(self, grids, system, limiter, bc, precision=32, rho=1.0, K=1.0, g=9.81,
                  cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, max_retries=8, stream=None,
-                 splitting="godunov"):
+                 splitting="godunov", dry_tol=1e-3):
         self.grids = [(tuple(int(v) for v in n), tuple(dx)) for n, dx in grids]
         self.ndim = len(self.grids[0][0])
         self.system = system
         self.m, self.mwaves = _nm(system, self.ndim)
         params = L.make_params(rho, K, g, cfl_desired, cfl_max, dt_max, precision, max_retries,
-                               splitting)
+                               splitting, dry_tol)
         self.h = L.claw_ensemble_create(self.grids, system, limiter, bc, params, stream)
 
     @classmethod
     def from_problems(cls, probs, precision=32, stream=None, **kw):
         p0 = probs[0]
         kw.setdefault("splitting", getattr(p0, "splitting", "godunov"))
+        kw.setdefault("dry_tol", getattr(p0, "dry_tol", 1e-3))
         e = cls([(p.n, p.dx) for p in probs], p0.system, p0.limiter, p0.bc, precision=precision,
                 rho=p0.rho, K=p0.K, g=p0.g, cfl_desired=p0.cfl_desired, cfl_max=p0.cfl_max,
                 stream=stream, **kw)
         for i, p in enumerate(probs):
             if p.system == "acoustics_var":
                 e.set_aux(i, p.rho_cell, p.K_cell)
-            if p.system == "shallow_water_bathy" and p.B_cell is not None:
+            if p.system in ("shallow_water_bathy", "shallow_water_dry") and p.B_cell is not None:
                 e.set_bathymetry(i, p.B_cell)
             e.set_q(i, p.q0)
         return e

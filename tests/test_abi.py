@@ -61,6 +61,8 @@ def _create(**over):
     (dict(n=(8, 8, 8), dx=(0.1, 0.1, 0.1), system="acoustics", m=4, mwaves=2,
           params=L.make_params(splitting="unsplit")), "unsplit update covers"),
     (dict(system="shallow_water_bathy", params=L.make_params(splitting="unsplit")), "unsplit update covers"),
+    (dict(system="shallow_water_dry", params=L.make_params(splitting="unsplit")), "unsplit update covers"),
+    (dict(system="shallow_water_dry", params=L.make_params(dry_tol=-1.0)), "dry_tol"),
     (dict(system="acoustics", m=3, mwaves=2, params=L.make_params(rho=0.0)), "rho and K"),
     (dict(system=7), "unknown system"),
     (dict(limiter=9), "unknown limiter"),
@@ -93,3 +95,32 @@ def test_null_solver_is_rejected():
     assert lib.claw_checkpoint(None) == L.CLAW_EINVAL
     assert lib.claw_rollback(None) == L.CLAW_EINVAL
     lib.claw_destroy(None)
+
+
+def declaration_comments():
+    """{function: the comment block that precedes its declaration} -- the
+    last comment before it, possibly across the other declarations of its
+    group."""
+    out = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        for m in re.finditer(r"^[a-z_ ]+\*?\s*\b(claw_[a-z0-9_]+)\s*\(", text, flags=re.M):
+            before = text[:m.start()]
+            end = before.rfind("*/")
+            start = before.rfind("/*", 0, end)
+            c = before[start:end] if end >= 0 else ""
+            out[m.group(1)] = re.sub(r"\s+", " ", re.sub(r"\n\s*\*", " ", c))
+    return out
+
+
+def test_every_declared_call_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each exported call's comment names the passage of the paper that
+    defines its operation (a section or an equation), or states that the
+    paper has no counterpart."""
+    comments = declaration_comments()
+    assert set(comments) == set(declared_functions())
+    missing = [n for n, c in comments.items()
+               if not re.search(r"\b(Sec\.|Eq\.|Table)|no counterpart", c)]
+    assert not missing, missing

@@ -244,6 +244,24 @@ def test_device_tensors_through_the_abi():
     assert fieldwise_linf(out.cpu().numpy(), ref["q"]) <= TOL64
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_pinned_host_buffers_through_the_abi(precision):
+    """Page-locked host buffers are read and written by the conversion kernels
+    directly (no device stage); the result equals the pageable path's."""
+    torch = pytest.importorskip("torch")
+    prob = inputs.random_problem("shallow_water", (75, 41), "mc", "wall", discontinuous=True)
+    with Solver.from_problem(prob, precision) as s:
+        s.run_steps(6)
+        want = s.get_q()
+    q_pin = torch.from_numpy(prob.q0.copy()).pin_memory()
+    out_pin = torch.full(prob.q0.shape, -7.0, dtype=torch.float64).pin_memory()
+    with Solver.from_problem(prob, precision) as s:
+        s.set_q(q_pin)
+        s.run_steps(6)
+        s.get_q(out_pin)
+    np.testing.assert_array_equal(out_pin.numpy(), want)
+
+
 # ------------------------------------------------------------------ faults
 
 def test_nan_state_is_reported():
