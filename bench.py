@@ -562,7 +562,8 @@ def slab_bench(args):
                                    f"{world} slabs along y, halo {2 * k} rows, {k} steps per refresh",
                        "parallelism": f"slab{world}", "segments": seg[:2],
                        "timing": "wall clock of the decomposed run: per period a halo refresh, a "
-                                 "speed pass, a state snapshot and one graph of fixed steps"},
+                                 "state snapshot and one graph of fixed steps (a speed pass before "
+                                 "the first period only)"},
             "periods": info.periods, "redone": info.redone, "cfl_max_seen": info.cfl_max_seen}),
             flush=True)
     if world > 1:
