@@ -355,6 +355,24 @@ claw_status claw_probe_fma(int precision, double* flops_per_s, void* cuda_stream
  * Rebuilds the tile lists. */
 claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
 
+/* Order in which a direction's persistent sweep takes its tiles: the most
+ * cells first (longest processing time first: balances uneven instances), or
+ * the tile list's own order (instance, then line groups, then segments along
+ * the lines). */
+typedef enum { CLAW_ORDER_LARGEST_FIRST = 0, CLAW_ORDER_LIST = 1 } claw_tile_order;
+
+/* Tile shape of direction d's sweep (Sec. 5.2: the block shape of each
+ * direction's kernel needs careful tuning): lines per tile (the kernel
+ * offers its full width and, except the two-line x sweep, half of it: 128
+ * or 64 lines; 0 keeps the current one), cells per line segment (>= 4,
+ * rounded up to whole 8-cell chunks; 0 keeps it) and the tile order (a
+ * claw_tile_order, -1 keeps it).  The result of a step does not depend on
+ * the shape beyond rounding (the first cells of a segment take separately
+ * compiled code).  Rebuilds the tile lists.  CLAW_EINVAL for an unoffered
+ * width. */
+claw_status claw_set_tile_shape(claw_solver* s, int d, int lines, int seg_len, int order);
+claw_status claw_get_tile_shape(claw_solver* s, int d, int* lines, int* seg_len, int* order);
+
 /* Autotuner (the tuning of tile shapes Sec. 5.2 calls for): for every direction, time trial_steps steps (CUDA events around
  * each sweep) twice with each candidate segment length and keep the fastest
  * (with CLAW_SPLIT_UNSPLIT: the rows per strip tile, timed on the unsplit
@@ -362,8 +380,10 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len);
  * candidates are fixed lengths plus, for w = 1..4, the shortest length whose
  * tiles fit in w waves of the CTAs the GPU holds at once; a second pass
  * tries the lengths that split the longest line into equal whole chunks
- * within a factor 1.5 of the first pass's best;
- * seg_out[d] (may be NULL) receives the choice.  The state, clock and step
+ * within a factor 1.5 of the first pass's best; this for each tile width
+ * the direction offers, then the tile order at the best shape;
+ * seg_out[d] (may be NULL) receives the segment length
+ * (claw_get_tile_shape gives the whole shape).  The state, clock and step
  * counters are restored afterwards, so the solution is unchanged.
  * Synchronises. */
 claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]);

@@ -77,6 +77,8 @@ _SIGS = {
     "claw_ensemble_size": [_vp],
     "claw_profile_steps": [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_long)],
     "claw_set_segment": [_vp, C.c_int, C.c_int],
+    "claw_set_tile_shape": [_vp, C.c_int, C.c_int, C.c_int, C.c_int],
+    "claw_get_tile_shape": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "claw_autotune": [_vp, C.c_int, C.POINTER(C.c_int)],
     "claw_probe_fma": [C.c_int, _dp, _vp],
     "claw_max_speed_noalloc": [C.POINTER(claw_grid), C.c_int, C.POINTER(C.c_int),
@@ -348,6 +350,21 @@ def claw_profile_steps(h, nsteps):
 
 def claw_set_segment(h, d, seg_len):
     _check(lib().claw_set_segment(h, int(d), int(seg_len)), "claw_set_segment")
+
+
+TILE_ORDERS = {"largest_first": 0, "list": 1}
+
+
+def claw_set_tile_shape(h, d, lines=0, seg_len=0, order=-1):
+    o = TILE_ORDERS[order] if isinstance(order, str) else int(order)
+    _check(lib().claw_set_tile_shape(h, int(d), int(lines), int(seg_len), o), "claw_set_tile_shape")
+
+
+def claw_get_tile_shape(h, d):
+    lines, seg, order = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().claw_get_tile_shape(h, int(d), C.byref(lines), C.byref(seg), C.byref(order)),
+           "claw_get_tile_shape")
+    return lines.value, seg.value, order.value
 
 
 def claw_probe_fma(precision, stream=None):

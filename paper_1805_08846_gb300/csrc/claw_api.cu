@@ -86,6 +86,8 @@ struct claw_solver {
     size_t stage_elems = 0;
     int seg[3] = {64, 64, 64};
     int tile_lines[3] = {kLines, kLines, kLines};   // lines per tile, from the sweep kernels
+    int narrow[3] = {0, 0, 0};                       // narrow tile width per direction
+    int tile_order[3] = {0, 0, 0};                   // CLAW_ORDER_* per direction
     std::vector<TileDesc> tiles[3];
     TileDesc* d_tiles[3] = {nullptr, nullptr, nullptr};
     std::vector<std::pair<int, int>> inst_tiles[3];  // [lo, hi) tile range per instance
@@ -179,8 +181,9 @@ claw_status build_tiles(claw_solver* s) {
             const int nl = d == 0 ? I.n[1] * I.n[2] : I.n[0];
             return (long long)std::min(s->tile_lines[d], nl - td.line0) * (td.b - td.a);
         };
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return cells(T[x]) > cells(T[y]); });
+        if (s->tile_order[d] == CLAW_ORDER_LARGEST_FIRST)
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int x, int y) { return cells(T[x]) > cells(T[y]); });
         if (s->d_order[d]) cudaFree(s->d_order[d]);
         s->d_order[d] = nullptr;
         CK(cudaMalloc(&s->d_order[d], sizeof(int) * std::max<size_t>(order.size(), 1)));
@@ -254,6 +257,7 @@ claw_status launch_sweep_range(claw_solver* s, int d, int tile_lo, int tile_hi, 
     L.speeds = speeds;
     L.grid = (unsigned)(tile_hi - tile_lo);
     L.stream = s->stream;
+    L.narrow = s->narrow[d];
     CK(launch_sweep(L));
     return CLAW_OK;
 }
@@ -269,6 +273,7 @@ claw_status resident_ctas(claw_solver* s, int d, int* out) {
     L.grid = 1;
     L.stream = s->stream;
     L.resident_out = out;
+    L.narrow = s->narrow[d];
     CK(launch_sweep(L));
     return CLAW_OK;
 }
@@ -487,6 +492,44 @@ claw_status encode_instance(claw_solver* s, int i, TmaSet& T) {
     return CLAW_OK;
 }
 
+// Lines per tile of direction d's sweep kernel at the solver's tile width
+// (tile lists and bulk-tensor boxes follow it).
+claw_status query_tile_lines(claw_solver* s, int d) {
+    SweepLaunch L{};
+    L.system = s->system;
+    L.limiter = s->limiter;
+    L.dir = d;
+    L.precision = s->precision;
+    L.grid = 1;
+    L.narrow = s->narrow[d];
+    L.lines_out = &s->tile_lines[d];
+    CK(launch_sweep(L));
+    return CLAW_OK;
+}
+
+// Lines per tile direction d's sweep would have at the given width.
+claw_status tile_lines_for(claw_solver* s, int d, int narrow, int* out) {
+    SweepLaunch L{};
+    L.system = s->system;
+    L.limiter = s->limiter;
+    L.dir = d;
+    L.precision = s->precision;
+    L.grid = 1;
+    L.narrow = narrow;
+    L.lines_out = out;
+    CK(launch_sweep(L));
+    return CLAW_OK;
+}
+
+// Bulk-tensor descriptors of every instance (their boxes follow the tile
+// widths) into the device copy.
+claw_status encode_all(claw_solver* s) {
+    std::vector<TmaSet> tma(s->B);
+    for (int i = 0; i < s->B; ++i) CKS(encode_instance(s, i, tma[i]));
+    CK(cudaMemcpy(s->d_tma, tma.data(), sizeof(TmaSet) * s->B, cudaMemcpyHostToDevice));
+    return CLAW_OK;
+}
+
 claw_status speed_pass(claw_solver* s, int i, int set_dt) {
     for (int d = 0; d < s->ndim; ++d) {
         auto r = s->inst_tiles[d][i];
@@ -591,29 +634,16 @@ claw_status create_impl(int B, const claw_grid* grids, int m, int mwaves, claw_s
     }
     s->stage_elems = max_cells * m;
     CK(cudaMalloc(&s->stage, s->stage_elems * sizeof(double)));
-    CK(cudaMalloc(&s->d_sums, 8 * sizeof(double)));
+    CK(cudaMalloc(&s->d_sums, 8 * (1 + kSumPartsMax) * sizeof(double)));   // sums, then partials
     CK(cudaMalloc(&s->d_counters, kMaxSweeps * sizeof(int)));
     CK(cudaMemsetAsync(s->d_counters, 0, kMaxSweeps * sizeof(int), s->stream));
     CK(cudaMalloc(&s->d_inst, sizeof(InstDesc) * B));
     CK(cudaMemcpyAsync(s->d_inst, s->inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s->stream));
     // Lines per tile of each direction's sweep kernel (tile lists and
     // bulk-tensor boxes follow it).
-    for (int d = 0; d < ndim; ++d) {
-        SweepLaunch L{};
-        L.system = s->system;
-        L.limiter = s->limiter;
-        L.dir = d;
-        L.precision = s->precision;
-        L.grid = 1;
-        L.lines_out = &s->tile_lines[d];
-        CK(launch_sweep(L));
-    }
-    {
-        std::vector<TmaSet> tma(B);
-        for (int i = 0; i < B; ++i) CKS(encode_instance(s, i, tma[i]));
-        CK(cudaMalloc(&s->d_tma, sizeof(TmaSet) * B));
-        CK(cudaMemcpy(s->d_tma, tma.data(), sizeof(TmaSet) * B, cudaMemcpyHostToDevice));
-    }
+    for (int d = 0; d < ndim; ++d) CKS(query_tile_lines(s, d));
+    CK(cudaMalloc(&s->d_tma, sizeof(TmaSet) * B));
+    CKS(encode_all(s));
 
     std::vector<Control> ctl(B);
     for (int i = 0; i < B; ++i) {
@@ -1074,6 +1104,40 @@ claw_status claw_set_segment(claw_solver* s, int d, int seg_len) {
     return build_tiles(s);
 }
 
+claw_status claw_set_tile_shape(claw_solver* s, int d, int lines, int seg_len, int order) {
+    CKS(check_solver(s));
+    if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
+    if (seg_len != 0 && seg_len < 4) return fail(CLAW_EINVAL, "segment length must be >= 4 (or 0: keep)");
+    if (order < -1 || order > CLAW_ORDER_LIST) return fail(CLAW_EINVAL, "unknown tile order %d", order);
+    int narrow = s->narrow[d];
+    if (lines != 0) {
+        int wide = 0, nar = 0;
+        CKS(tile_lines_for(s, d, 0, &wide));
+        CKS(tile_lines_for(s, d, 1, &nar));
+        if (lines == wide) narrow = 0;
+        else if (lines == nar) narrow = 1;
+        else return fail(CLAW_EINVAL, "direction %d offers %d or %d lines per tile (got %d)", d, wide, nar, lines);
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    if (narrow != s->narrow[d]) {
+        s->narrow[d] = narrow;
+        CKS(query_tile_lines(s, d));
+        CKS(encode_all(s));
+    }
+    if (seg_len != 0) s->seg[d] = (seg_len + 7) / 8 * 8;   // whole chunks, as claw_set_segment
+    if (order >= 0) s->tile_order[d] = order;
+    return build_tiles(s);
+}
+
+claw_status claw_get_tile_shape(claw_solver* s, int d, int* lines, int* seg_len, int* order) {
+    CKS(check_solver(s));
+    if (d < 0 || d >= s->ndim) return fail(CLAW_EINVAL, "direction %d out of range", d);
+    if (lines) *lines = s->tile_lines[d];
+    if (seg_len) *seg_len = s->seg[d];
+    if (order) *order = s->tile_order[d];
+    return CLAW_OK;
+}
+
 claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
     CKS(check_solver(s));
     if (trial_steps < 1) return fail(CLAW_EINVAL, "trial_steps must be >= 1");
@@ -1122,60 +1186,91 @@ claw_status claw_autotune(claw_solver* s, int trial_steps, int seg_out[3]) {
     for (int d = 0; d < s->ndim && st == CLAW_OK && !s->unsplit; ++d) {
         int maxN = 0;
         for (int i = 0; i < s->B; ++i) maxN = std::max(maxN, s->inst[i].n[d]);
-        // Fixed lengths, plus for w = 1..4 the shortest segment whose tiles
-        // fill at most w waves of resident CTAs (a persistent sweep whose
-        // tiles are few and even ends without a partial last wave).
-        std::vector<int> cand(d == 0 ? cand_x : cand_t, (d == 0 ? cand_x : cand_t) + 9);
-        int resident = 0;
-        st = resident_ctas(s, d, &resident);
+        // Tile widths the sweep offers (lines per tile), each searched over
+        // segment lengths; then the tile order at the best shape.
+        int widths[2] = {0, 0}, nw = 0;
+        st = tile_lines_for(s, d, 0, &widths[nw++]);
+        if (st == CLAW_OK) st = tile_lines_for(s, d, 1, &widths[nw]);
         if (st != CLAW_OK) break;
-        for (int w = 1; w <= 4; ++w) {
-            int lo = 8, hi = (maxN + 7) / 8 * 8;
-            if (tiles_for_segment(s, d, hi) > (long long)w * resident) continue;
-            while (lo < hi) {   // smallest multiple of 8 with few enough tiles
-                const int mid = (lo / 8 + hi / 8) / 2 * 8;
-                if (tiles_for_segment(s, d, mid) <= (long long)w * resident) hi = mid;
-                else lo = mid + 8;
-            }
-            cand.push_back(lo);
-        }
-        std::sort(cand.begin(), cand.end());
-        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        if (widths[1] != widths[0]) ++nw;
         double best_ms = 1e30;
-        std::vector<int> tried;
-        auto trial = [&](int L) -> claw_status {
-            if (std::find(tried.begin(), tried.end(), L) != tried.end()) return CLAW_OK;
-            tried.push_back(L);
-            CKS(claw_set_segment(s, d, L));
-            // best of two trials from the same state (the first also warms
-            // caches and the new tile lists)
-            for (int rep = 0; rep < 2; ++rep) {
-                double ms[4], tot;
-                long nl;
-                CKS(claw_profile_steps(s, trial_steps, ms, &tot, &nl));
-                if (ms[d] < best_ms) {
-                    best_ms = ms[d];
-                    best[d] = s->seg[d];
+        int best_lines = s->tile_lines[d];
+        for (int wi = 0; wi < nw && st == CLAW_OK; ++wi) {
+            st = claw_set_tile_shape(s, d, widths[wi], 0, CLAW_ORDER_LARGEST_FIRST);
+            if (st != CLAW_OK) break;
+            // Fixed lengths, plus for w = 1..4 the shortest segment whose tiles
+            // fill at most w waves of resident CTAs (a persistent sweep whose
+            // tiles are few and even ends without a partial last wave).
+            std::vector<int> cand(d == 0 ? cand_x : cand_t, (d == 0 ? cand_x : cand_t) + 9);
+            int resident = 0;
+            st = resident_ctas(s, d, &resident);
+            if (st != CLAW_OK) break;
+            for (int w = 1; w <= 4; ++w) {
+                int lo = 8, hi = (maxN + 7) / 8 * 8;
+                if (tiles_for_segment(s, d, hi) > (long long)w * resident) continue;
+                while (lo < hi) {   // smallest multiple of 8 with few enough tiles
+                    const int mid = (lo / 8 + hi / 8) / 2 * 8;
+                    if (tiles_for_segment(s, d, mid) <= (long long)w * resident) hi = mid;
+                    else lo = mid + 8;
                 }
-                CKS(restore());
+                cand.push_back(lo);
             }
-            return CLAW_OK;
-        };
-        for (size_t k = 0; k < cand.size() && st == CLAW_OK; ++k) {
-            if (cand[k] > 2 * maxN && k > 0) break;
-            st = trial(cand[k]);
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            double width_best = 1e30;
+            int width_seg = s->seg[d];
+            std::vector<int> tried;
+            auto trial = [&](int L) -> claw_status {
+                if (std::find(tried.begin(), tried.end(), L) != tried.end()) return CLAW_OK;
+                tried.push_back(L);
+                CKS(claw_set_segment(s, d, L));
+                // best of two trials from the same state (the first also warms
+                // caches and the new tile lists)
+                for (int rep = 0; rep < 2; ++rep) {
+                    double ms[4], tot;
+                    long nl;
+                    CKS(claw_profile_steps(s, trial_steps, ms, &tot, &nl));
+                    if (ms[d] < width_best) {
+                        width_best = ms[d];
+                        width_seg = s->seg[d];
+                    }
+                    CKS(restore());
+                }
+                return CLAW_OK;
+            };
+            for (size_t k = 0; k < cand.size() && st == CLAW_OK; ++k) {
+                if (cand[k] > 2 * maxN && k > 0) break;
+                st = trial(cand[k]);
+            }
+            // Second pass: lengths that split the longest line into equal whole
+            // chunks (k segments, no short tail), within a factor 1.5 of the
+            // first pass's best.
+            const int b0 = width_seg;
+            for (int k = 1; k <= 256 && st == CLAW_OK; ++k) {
+                const int L = ((maxN + k - 1) / k + 7) / 8 * 8;
+                if (L < 8) break;
+                if (2 * L > 3 * b0 || 3 * L < 2 * b0) continue;
+                st = trial(L);
+            }
+            if (st == CLAW_OK && width_best < best_ms) {
+                best_ms = width_best;
+                best[d] = width_seg;
+                best_lines = widths[wi];
+            }
         }
-        // Second pass: lengths that split the longest line into equal whole
-        // chunks (k segments, no short tail), within a factor 1.5 of the
-        // first pass's best.
-        const int b0 = best[d];
-        for (int k = 1; k <= 256 && st == CLAW_OK; ++k) {
-            const int L = ((maxN + k - 1) / k + 7) / 8 * 8;
-            if (L < 8) break;
-            if (2 * L > 3 * b0 || 3 * L < 2 * b0) continue;
-            st = trial(L);
+        if (st == CLAW_OK) st = claw_set_tile_shape(s, d, best_lines, best[d], CLAW_ORDER_LARGEST_FIRST);
+        // the tile list in its own order (instance, then row / column groups,
+        // then segments) instead of largest first
+        double list_ms = 1e30;
+        if (st == CLAW_OK) st = claw_set_tile_shape(s, d, 0, 0, CLAW_ORDER_LIST);
+        for (int rep = 0; rep < 2 && st == CLAW_OK; ++rep) {
+            double ms[4], tot;
+            long nl;
+            st = claw_profile_steps(s, trial_steps, ms, &tot, &nl);
+            if (st == CLAW_OK) st = restore();
+            list_ms = std::min(list_ms, ms[d]);
         }
-        if (st == CLAW_OK) st = claw_set_segment(s, d, best[d]);
+        if (st == CLAW_OK && list_ms >= best_ms) st = claw_set_tile_shape(s, d, 0, 0, CLAW_ORDER_LARGEST_FIRST);
     }
     cudaStreamSynchronize(s->stream);
     cudaFree(saved);

@@ -274,24 +274,43 @@ __global__ void aux_const_kernel(Real* aux, InstDesc I, double rho, double K) {
     }
 }
 
-// Deterministic FP64 field sums: one CTA per field, each thread a fixed
-// strided subsequence, then a fixed shared-memory tree.
+// Deterministic FP64 field sums in two passes with a fixed shape: kSumParts
+// CTAs per field each sum a fixed strided subset of the cells (every thread a
+// fixed subsequence, then a fixed shared-memory tree) into a partial, and
+// one CTA per field adds its partials in a fixed tree.  The same grid and
+// state give the same bits on every call.
+constexpr int kSumParts = 152;
+constexpr int kSumThreads = 512;
+
 template <class Real>
-__global__ void __launch_bounds__(1024) sums_kernel(const Real* pool, InstDesc I, const Control* ctl,
-                                                    double* out) {
-    __shared__ double part[1024];
-    const int f = blockIdx.x;
+__global__ void __launch_bounds__(kSumThreads) sums_part_kernel(const Real* pool, InstDesc I, const Control* ctl,
+                                                               double* partial) {
+    __shared__ double part[kSumThreads];
+    const int f = blockIdx.y;
     const long long nx = I.n[0];
     const long long ncell = nx * I.n[1] * I.n[2];
     const Real* q = pool + I.offset + ctl->cur[f] * I.vstride + f * I.fstride;
     double acc = 0.0;
-    for (long long idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
+    for (long long idx = (long long)blockIdx.x * kSumThreads + threadIdx.x; idx < ncell;
+         idx += (long long)kSumParts * kSumThreads) {
         const long long row = idx / nx, x = idx - row * nx;
         acc += (double)q[row * I.pitch + x];
     }
     part[threadIdx.x] = acc;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[f * kSumParts + blockIdx.x] = part[0];
+}
+
+__global__ void __launch_bounds__(256) sums_final_kernel(const double* partial, double* out) {
+    __shared__ double part[256];
+    const int f = blockIdx.x;
+    part[threadIdx.x] = (int)threadIdx.x < kSumParts ? partial[f * kSumParts + threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
         __syncthreads();
     }
@@ -362,10 +381,14 @@ cudaError_t launch_aux_plane(int precision, void* aux, const InstDesc& I, int k,
 
 cudaError_t launch_sums(int precision, const void* pool, const InstDesc& I, const Control* ctl,
                         int m, double* out, cudaStream_t st) {
+    static_assert(kSumParts <= 256, "the final pass adds at most 256 partials");
+    double* partial = out + 8;   // the caller's buffer holds 8 sums, then 8 x kSumParts partials
+    const dim3 grid(kSumParts, m);
     if (precision == 64)
-        sums_kernel<double><<<m, 1024, 0, st>>>((const double*)pool, I, ctl, out);
+        sums_part_kernel<double><<<grid, kSumThreads, 0, st>>>((const double*)pool, I, ctl, partial);
     else
-        sums_kernel<float><<<m, 1024, 0, st>>>((const float*)pool, I, ctl, out);
+        sums_part_kernel<float><<<grid, kSumThreads, 0, st>>>((const float*)pool, I, ctl, partial);
+    sums_final_kernel<<<m, 256, 0, st>>>(partial, out);
     return cudaGetLastError();
 }
 

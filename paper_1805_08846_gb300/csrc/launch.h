@@ -25,6 +25,7 @@ struct SweepLaunch {
     int* resident_out;   // non-null: report the CTAs the GPU holds at once, launch nothing
     int* chunk_out;      // non-null: report the cells per staged chunk, launch nothing
     int* lines_out;      // non-null: report the lines per tile, launch nothing
+    int narrow;          // 1: the narrow tile width (half the lines per tile), where offered
 };
 
 // Record the thread-local message claw_last_error() returns.
@@ -83,6 +84,8 @@ cudaError_t launch_aux_const(int precision, void* aux, const InstDesc& I, double
 // One material plane (FP64 values, x fastest, no padding) into plane k.
 cudaError_t launch_aux_plane(int precision, void* aux, const InstDesc& I, int k, const double* src,
                              cudaStream_t st);
+// out: 8 doubles for the sums followed by room for 8 x kSumPartsMax partials.
+constexpr int kSumPartsMax = 256;
 cudaError_t launch_sums(int precision, const void* pool, const InstDesc& I, const Control* ctl,
                         int m, double* out, cudaStream_t st);
 

@@ -266,12 +266,35 @@ struct ShallowWater {
         w.W[2][1] = a3 * s3;
         w.W[2][2] = a3 * vh;
 
+        const Real km2 = vmin(uh, Real(0)), kp2 = vmax(uh, Real(0));
+        const Real ng = Real(0) - P.g;
+        {
+            // The whole warp subcritical at this interface (|u_hat| < c_hat,
+            // so s1 < 0 < s3, and both middle states subcritical, so no
+            // transonic wave): the 1-wave goes left and the 3-wave right, and
+            // no split factor is needed (a warp vote keeps the branch uniform;
+            // measured at 4096^2: x sweep 0.134 -> 0.128 ms, y 0.106 -> 0.100 ms).
+            // The solver is called by every lane of a warp.
+            const Real hm1 = l.q[0] + w.W[0][0], hum1 = l.q[1] + w.W[0][1];
+            const Real hm3 = r.q[0] - w.W[2][0], hum3 = r.q[1] - w.W[2][1];
+            const Real sup1 = vfma(hum1, hum1, (ng * hm1) * (hm1 * hm1));
+            const Real sup3 = vfma(hum3, hum3, (ng * hm3) * (hm3 * hm3));
+            const bool lane_sub = !any(!vlt(vabs(uh), ch)) && !any(vgt(sup1, Real(0))) && !any(vgt(sup3, Real(0)));
+            if (__all_sync(0xffffffffu, lane_sub)) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    w.amdq[c] = s1 * w.W[0][c];
+                    w.apdq[c] = s3 * w.W[2][c];
+                }
+                w.amdq[2] = vfma(s1, w.W[0][2], km2 * w.W[1][2]);
+                w.apdq[2] = vfma(s3, w.W[2][2], kp2 * w.W[1][2]);
+                return;
+            }
+        }
         // Split factors: A-dQ = sum km_p W_p, A+dQ = sum kp_p W_p.
         Real km1 = vmin(s1, Real(0)), kp1 = vmax(s1, Real(0));
         Real km3 = vmin(s3, Real(0)), kp3 = vmax(s3, Real(0));
-        const Real km2 = vmin(uh, Real(0)), kp2 = vmax(uh, Real(0));
 
-        const Real ng = Real(0) - P.g;
         // Transonic tests.  The middle state must be supercritical for either
         // wave to be transonic (hu_m^2 > g h_m^3), which subcritical flow never
         // is: that one packed quantity is tested first, the other three

@@ -180,13 +180,22 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
 // 32 bytes of each of 128 rows, kept with the 32-byte swizzle (the two
 // 16-byte halves of a row swap places on bit 2 of the row) so that a warp's
 // 16-byte reads of its own rows hit every bank once.
-template <class Sys, class Real, int DIR>
+// Tile widths a direction's sweep offers (the autotuner picks one): NARROW
+// halves the lines per tile (fewer lanes past the edge of small or uneven
+// grids, more tiles); the two-line x sweep has only its 64-row tiles.
+template <class Sys, int DIR>
+constexpr bool narrow_offered() {
+    return !(Lanes<typename Sys::Value>::N == 2 && DIR == 0);
+}
+
+template <class Sys, class Real, int DIR, bool NARROW = false>
 struct StageCfg {
     // lines per thread: 2 when the system computes on f2 (two FP32 lines)
     static constexpr int PK = Lanes<typename Sys::Value>::N;
     // lines per tile: 128, or 64 for the two-line x sweep (one-warp CTAs
-    // whose three-stage ring is small enough for 11 CTAs per SM)
-    static constexpr int LINES = (PK == 2 && DIR == 0) ? kLines / 2 : kLines;
+    // whose three-stage ring is small enough for 11 CTAs per SM); a narrow
+    // tile has half as many
+    static constexpr int LINES = (PK == 2 && DIR == 0) ? kLines / 2 : (NARROW ? kLines / 2 : kLines);
     static constexpr int NT = LINES / PK;                       // threads per CTA
     static constexpr int NP = Sys::NQ + Sys::NA;               // planes per chunk
     static constexpr int C = 32 / (int)sizeof(Real);            // cells per chunk
@@ -205,13 +214,15 @@ struct StageCfg {
     // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
     // a 5-CTA budget forces worse schedules), 2 for FP64; 6 CTAs of 64
     // two-line threads for the packed form (7 fit at run time)
-    static constexpr int MIN_CTAS = PK == 2 ? (DIR == 0 ? 12 : 6) : (sizeof(Real) == 4 ? 4 : 2);
+    // (the same per-SM budget for narrow tiles: twice as many CTAs)
+    static constexpr int MIN_CTAS =
+        (PK == 2 ? (DIR == 0 ? 12 : 6) : (sizeof(Real) == 4 ? 4 : 2)) * ((NARROW && !(PK == 2 && DIR == 0)) ? 2 : 1);
 };
 
-template <class Sys, class Real, int LIM, int DIR>
-__global__ void __launch_bounds__((StageCfg<Sys, Real, DIR>::NT), (StageCfg<Sys, Real, DIR>::MIN_CTAS))
+template <class Sys, class Real, int LIM, int DIR, bool NARROW>
+__global__ void __launch_bounds__((StageCfg<Sys, Real, DIR, NARROW>::NT), (StageCfg<Sys, Real, DIR, NARROW>::MIN_CTAS))
     sweep_kernel(const SweepArgs A, const typename Sys::Params P) {
-    using Cfg = StageCfg<Sys, Real, DIR>;
+    using Cfg = StageCfg<Sys, Real, DIR, NARROW>;
     using V = typename Sys::Value;     // Real, or f2 for two lines per thread
     constexpr int PK = Cfg::PK;
     using Cell = typename Sys::Cell;

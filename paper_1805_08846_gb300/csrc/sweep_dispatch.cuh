@@ -6,10 +6,10 @@
 
 namespace claw {
 
-template <class Sys, class Real, int LIM, int DIR>
-cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
+template <class Sys, class Real, int LIM, int DIR, bool NARROW>
+cudaError_t sweep_go_w(const SweepLaunch& L, const typename Sys::Params& P) {
     if (L.grid == 0) return cudaSuccess;
-    using Cfg = StageCfg<Sys, Real, DIR>;
+    using Cfg = StageCfg<Sys, Real, DIR, NARROW>;
     if (L.chunk_out || L.lines_out) {
         if (L.chunk_out) *L.chunk_out = Cfg::C;
         if (L.lines_out) *L.lines_out = Cfg::LINES;
@@ -17,16 +17,16 @@ cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     }
     static int resident = 0;   // CTAs of this kernel the whole GPU holds at once
     if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR, NARROW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
         // all of L1 that can be shared memory: the resident CTA count is set
         // by the staging rings, not left to the driver's default split
-        e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR>,
+        e = cudaFuncSetAttribute(sweep_kernel<Sys, Real, LIM, DIR, NARROW>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR>, Cfg::NT,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Sys, Real, LIM, DIR, NARROW>, Cfg::NT,
                                                           Cfg::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
@@ -39,8 +39,17 @@ cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
     }
     unsigned grid = L.grid;
     if (L.args.persistent && grid > (unsigned)resident) grid = (unsigned)resident;
-    sweep_kernel<Sys, Real, LIM, DIR><<<grid, Cfg::NT, Cfg::SMEM, L.stream>>>(L.args, P);
+    sweep_kernel<Sys, Real, LIM, DIR, NARROW><<<grid, Cfg::NT, Cfg::SMEM, L.stream>>>(L.args, P);
     return cudaGetLastError();
+}
+
+// The tile width: narrow (half the lines per tile) where the sweep offers it.
+template <class Sys, class Real, int LIM, int DIR>
+cudaError_t sweep_go(const SweepLaunch& L, const typename Sys::Params& P) {
+    if constexpr (narrow_offered<Sys, DIR>()) {
+        if (L.narrow) return sweep_go_w<Sys, Real, LIM, DIR, true>(L, P);
+    }
+    return sweep_go_w<Sys, Real, LIM, DIR, false>(L, P);
 }
 
 template <class Sys, class Real, int DIR>

@@ -122,6 +122,13 @@ class Solver:
     def set_segment(self, d, seg_len):
         L.claw_set_segment(self.h, d, seg_len)
 
+    def set_tile_shape(self, d, lines=0, seg_len=0, order=-1):
+        L.claw_set_tile_shape(self.h, d, lines, seg_len, order)
+
+    def tile_shape(self, d):
+        """(lines per tile, segment length, order) of direction d."""
+        return L.claw_get_tile_shape(self.h, d)
+
     def autotune(self, trial_steps=3):
         return L.claw_autotune(self.h, trial_steps)
 
@@ -198,6 +205,12 @@ class Ensemble:
 
     def set_segment(self, d, seg_len):
         L.claw_set_segment(self.h, d, seg_len)
+
+    def set_tile_shape(self, d, lines=0, seg_len=0, order=-1):
+        L.claw_set_tile_shape(self.h, d, lines, seg_len, order)
+
+    def tile_shape(self, d):
+        return L.claw_get_tile_shape(self.h, d)
 
     def autotune(self, trial_steps=3):
         return L.claw_autotune(self.h, trial_steps)

@@ -134,6 +134,65 @@ def test_autotune_keeps_state_and_clock(precision):
         check_fp32(prob, q, ref["q"])
 
 
+SHAPE_CASES = [("shallow_water", (131, 97), "mc", ("extrap", "wall", "periodic", "periodic")),
+               ("acoustics", (130, 67), "minmod", "wall"),
+               ("acoustics_var", (75, 40, 33), "mc", ("periodic", "wall", "extrap", "wall", "wall", "extrap")),
+               ("shallow_water_dry", (97, 70), "mc", "wall")]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("system,shape,limiter,bc", SHAPE_CASES)
+def test_tile_shapes_and_orders_give_the_same_result(system, shape, limiter, bc, precision):
+    """Narrow tiles (64 lines where the sweep offers them), short segments
+    and either tile order change which CTA marches which line and where its
+    segments start (the first cells of a segment are solved by separately
+    compiled code, so the last bit may differ): every shape matches the
+    oracle, and the shapes agree with each other to rounding."""
+    prob = inputs.random_problem(system, shape, limiter, bc, discontinuous=True)
+    ref = Oracle(prob).run_steps(prob.q0, 6)
+    got = []
+    for lines, seg, order in ((0, 0, 0), (64, 24, 0), (64, 40, 1), (0, 16, 1)):
+        with Solver.from_problem(prob, precision=precision) as s:
+            for d in range(prob.ndim):
+                s.set_tile_shape(d, lines, seg, order)
+                if lines:
+                    assert s.tile_shape(d)[0] == 64
+            s.run_steps(6)
+            got.append(s.get_q())
+    for q in got:
+        if precision == 64:
+            assert fieldwise_linf(q, ref["q"]) <= TOL64
+            assert fieldwise_linf(q, got[0]) <= 1e-14
+        else:
+            check_fp32(prob, q, ref["q"])
+            assert max(oracle.rel_l2(q[f], got[0][f]) for f in range(q.shape[0])
+                       if np.abs(got[0][f]).max() > 0) <= 1e-6
+
+
+def test_tile_shape_rejects_unoffered_widths():
+    prob = inputs.random_problem("shallow_water", (40, 30), "mc", "wall")
+    with Solver.from_problem(prob, precision=32) as s:
+        with pytest.raises(ClawError):
+            s.set_tile_shape(0, 128)          # the two-line x sweep has only 64-row tiles
+        with pytest.raises(ClawError):
+            s.set_tile_shape(1, 96)
+        s.set_tile_shape(1, 64, 0, "list")
+        assert s.tile_shape(1) == (64, 64, 1)
+
+
+def test_narrow_tiles_in_an_uneven_ensemble():
+    probs = inputs.sw_ensemble(B=5, nmin=20, nmax=150, nsteps=8)
+    refs = [Oracle(p).run_steps(p.q0, 8)["q"] for p in probs]
+    e = Ensemble.from_problems(probs, precision=32)
+    try:
+        e.set_tile_shape(1, 64, 0, "list")
+        e.run_steps(8)
+        for i, p in enumerate(probs):
+            check_fp32(p, e.get_q(i), refs[i])
+    finally:
+        e.close()
+
+
 def test_initial_dt_from_speed_pass():
     prob = inputs.sw_radial_dam_break(96)
     M = Oracle(prob).max_speed_over_dx(prob.q0)
