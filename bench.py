@@ -33,11 +33,11 @@ METRIC = "cell-updates/s"
 # Algorithmic flops of one shallow-water cell per sweep: the paper's Nsight
 # count of 313 flop per cell-step over its two sweeps (Tables 1-2 give the
 # per-sweep MFlop at 1024^2).  Our FP32 sweep executes 158.7 per cell; the
-# FP64 x sweep executes 292.8 (2 per DFMA, 1 per DADD / DMUL: the double
-# reciprocal square roots, divides and limiter ratios expand into FMA
+# FP64 x sweep executes 197.1 (2 per DFMA, 1 per DADD / DMUL: the double
+# reciprocal square roots and the Newton reciprocals expand into FMA
 # sequences) -- both counted with ncu, see profiles/.
 SW_FLOP_PER_CELL_SWEEP = 313.0 / 2.0
-FP64_EXECUTED_DFLOP = 292.8
+FP64_EXECUTED_DFLOP = 197.1
 
 
 # Files the FP32 shallow-water sweep kernels are compiled from (the unit

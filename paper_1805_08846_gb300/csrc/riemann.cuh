@@ -48,18 +48,39 @@ __device__ __forceinline__ bool finite_(Real x) {
     return fabs(x) <= (Real)INFINITY && x == x;
 }
 
+// FP64 reciprocal by the Newton-Raphson iteration for 1/d,
+//   e = 1 - d r,  r <- r + r e   (the relative error e squares each step),
+// started from the hardware's approximate reciprocal (PTX rcp.approx.ftz.f64;
+// measured on GB300 over 6.7e7 random normal d: relative error <= 9.9e-7
+// before the steps, <= 9.9e-13 after one, and after two the correctly rounded
+// 1/d on every one of them).  A subnormal d counts as 0 (an infinite start, a
+// NaN result), as does d = 0: callers use it where d is a normal positive
+// number or where a NaN ratio is harmless (the limiter ratio of a zero wave).
+// Against the correctly rounded divide it took the 4096^2 FP64 shallow-water
+// sweep from 5.63 to 4.27 ms and the 512^3 FP64 acoustics sweep from 18.8 to
+// 17.2 ms.  (The same two steps for the reciprocal square root, from
+// rsqrt.approx.ftz.f64, were slower than the library's rsqrt: 4.38 ms.)
+__device__ __forceinline__ double rcp_nr(double d) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Division, reciprocal and square roots.  FP64 (the plain path) uses the
-// correctly rounded divide, reciprocal and square root, and the double
-// reciprocal square root (a few ulp) where a solver asks for one; the FP32
-// form uses the SFU approximations (reciprocal and reciprocal square root, a
-// few ulp), far inside its 1e-4 / 1e-5 error budget and a fraction of the
-// instruction count.
+// correctly rounded divide (the rare entropy-fix ratios) and square root, the
+// Newton reciprocal above and the double reciprocal square root (a few ulp)
+// where a solver asks for one; the FP32 form uses the SFU approximations
+// (reciprocal and reciprocal square root, a few ulp), far inside its
+// 1e-4 / 1e-5 error budget and a fraction of the instruction count.
 template <class Real>
 struct Ops;
 template <>
 struct Ops<double> {
     __device__ __forceinline__ static double div(double a, double b) { return a / b; }
-    __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }
+    __device__ __forceinline__ static double rcp(double x) { return rcp_nr(x); }
     __device__ __forceinline__ static double rsqrt(double x) { return ::rsqrt(x); }
     __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
 };
@@ -519,9 +540,17 @@ struct ShallowWaterDry {
 
     __device__ __forceinline__ static void prepare(Cell& cell, const Params& P) {
         const bool wet = cell.q[0] > P.dry_tol;
-        const Real rh = wet ? Ops<Real>::rcp(cell.q[0]) : Real(0);
+        const Real rh = wet ? rcp_(cell.q[0]) : Real(0);
         cell.u = cell.q[1] * rh;
         cell.v = cell.q[2] * rh;
+    }
+
+    // 1/h of a wet cell.  FP64: the correctly rounded reciprocal (with
+    // dry_tol = 0 a thin film may be subnormal, which the Newton reciprocal
+    // counts as 0)
+    __device__ __forceinline__ static Real rcp_(Real x) {
+        if constexpr (kFast) return Ops<Real>::rcp(x);
+        else return Real(1) / x;
     }
 
     __device__ __forceinline__ static Real gsqrt(Real gh) {
@@ -557,7 +586,7 @@ struct ShallowWaterDry {
             cr = wr ? sqrt(P.g * hr) : Real(0);
             ch = sqrt(P.g * (Real(0.5) * (hl + hr)));
         }
-        uh = Ops<Real>::div(sql * l.u + sqr * r.u, sql + sqr);
+        uh = (sql * l.u + sqr * r.u) * Ops<Real>::rcp(sql + sqr);
         const Real lm = wl ? l.u - cl : r.u - Real(2) * cr;
         const Real rp = wr ? r.u + cr : l.u + Real(2) * cl;
         s1 = fmin(uh - ch, lm);
@@ -592,6 +621,8 @@ struct ShallowWaterDry {
         const Real qr[3] = {hr, hr * r.u, hr * r.v};
         const Real fl[3] = {ql[1], ql[1] * l.u + P.half_g * hl * hl, ql[1] * l.v};
         const Real fr[3] = {qr[1], qr[1] * r.u + P.half_g * hr * hr, qr[1] * r.v};
+        // s3 - s1 >= 2 c_hat and sql + sqr >= sqrt(h) of a wet side: normal
+        // numbers even for a subnormal depth, so the Newton reciprocal holds
         const Real inv = Ops<Real>::rcp(s3 - s1);
         const bool shore = !(hl > Real(0)) || !(hr > Real(0));
 #pragma unroll
@@ -645,7 +676,8 @@ __device__ __forceinline__ Real limiter_phi(Real theta) {
 // phi(num / den) for den >= 0.  FP32: a saturating multiply by the SFU
 // reciprocal -- minmod is sat(theta); MC is 2 sat(min(theta, (1 + theta)/4)),
 // the same function written around the clamp to [0, 1] (a NaN ratio of a
-// zero wave saturates to 0).  FP64: the correctly rounded ratio.
+// zero wave saturates to 0).  FP64: num times the Newton reciprocal of den
+// (within 2 ulp of the ratio; a zero wave gives NaN, as 0/0 does).
 template <int LIM, class Real>
 __device__ __forceinline__ Real limiter_ratio(Real num, Real den) {
     if constexpr (std::is_same<Real, f2>::value) {
@@ -656,7 +688,7 @@ __device__ __forceinline__ Real limiter_ratio(Real num, Real den) {
         if (LIM == kLimMC) return 2.0f * __saturatef(fminf(theta, 0.25f + 0.25f * theta));
         return 1.0f;
     } else {
-        return limiter_phi<LIM, Real>(num / den);
+        return limiter_phi<LIM, Real>(num * rcp_nr(den));
     }
 }
 
