@@ -343,6 +343,20 @@ def test_negative_depth_is_reported():
     assert ei.value.status == L.CLAW_ENONPHYS
 
 
+def test_subnormal_fp32_depth_is_reported():
+    """FP32 shallow water: a depth below the smallest normal float reads as 0
+    in the flush-to-zero reciprocal square root, so the step is reported as
+    non-physical (like h <= 0) instead of marching on a meaningless film."""
+    prob = inputs.random_problem("shallow_water", (20, 20), "minmod", "wall")
+    q = prob.q0.copy()
+    q[0, 3, 4] = 1e-40          # subnormal once converted to FP32
+    q[1, 3, 4] = q[2, 3, 4] = 0.0
+    with pytest.raises(ClawError) as ei:
+        with Solver.from_problem(prob.with_(q0=q), 32) as s:
+            s.run_steps(2)
+    assert ei.value.status == L.CLAW_ENONPHYS
+
+
 def test_repeated_cfl_rejection_is_reported():
     """cfl_desired above cfl_max can never be kept: after max_retries
     consecutive rejections the run stops with CLAW_ECFL."""
