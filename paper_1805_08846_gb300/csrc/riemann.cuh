@@ -91,8 +91,9 @@ struct Ops<double> {
 // took the 4096^2 FP32 shallow-water sweeps from 139 / 125 to 113 / 100
 // instructions per cell (x 0.128 -> 0.119 ms, y 0.0995 -> 0.089 ms).  A
 // shallow-water depth below the smallest normal float (1.2e-38) then reads as
-// 0: its speeds turn non-finite and the step control reports it as
-// non-physical, which such a depth is.
+// 0: in the Roe solvers its speeds turn non-finite and the step control
+// reports it as non-physical, which such a depth is; the wet/dry solver
+// counts it as dry.
 __device__ __forceinline__ float rcp_ftz(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -564,15 +565,17 @@ struct ShallowWaterDry {
         cell.v = cell.q[2] * rh;
     }
 
-    // 1/h and sqrt(h) of a wet depth, which may be subnormal when dry_tol is
-    // 0: FP64 the correctly rounded reciprocal (the Newton reciprocal counts a
-    // subnormal as 0), FP32 the SFU forms that keep subnormal operands
+    // 1/h and sqrt(h) of a wet depth.  FP64: the correctly rounded
+    // reciprocal (with dry_tol = 0 a wet depth may be subnormal, which the
+    // Newton reciprocal counts as 0).  FP32: the flush-to-zero SFU forms; the
+    // FP32 launcher raises dry_tol to at least the smallest normal float, so
+    // a wet depth is never subnormal there.
     __device__ __forceinline__ static Real rcp_(Real x) {
-        if constexpr (kFast) return __fdividef(Real(1), x);
+        if constexpr (kFast) return Ops<Real>::rcp(x);
         else return Real(1) / x;
     }
     __device__ __forceinline__ static Real sqrt_(Real x) {   // x > 0
-        if constexpr (kFast) return x * rsqrtf(x);
+        if constexpr (kFast) return Ops<Real>::sqrt_(x);
         else return sqrt(x);
     }
 
