@@ -544,12 +544,11 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR, NARROW>::NT), (Stage
                         : (jj * Cfg::LINES + line) * (int)sizeof(Real);
     };
     auto stage_of = [&](int kk) { return smem + ((kbase + kk) % STAGES) * Cfg::STAGE_BYTES; };
-    auto put_stage = [&](int i, const V* qn) {
-        const int rel = i - a;
-        unsigned char* st = stage_of(rel / C);
+    // result of the cell at position jj of the chunk held by stage st
+    auto put_stage = [&](unsigned char* st, int jj, const V* qn) {
 #pragma unroll
         for (int k = 0; k < PK; ++k) {
-            unsigned char* sk = st + pos_off(line_of(k), rel % C);
+            unsigned char* sk = st + pos_off(line_of(k), jj);
 #pragma unroll
             for (int c = 0; c < NQ; ++c) *reinterpret_cast<Real*>(sk + c * Cfg::BOX) = lane_of(qn[c], k);
         }
@@ -577,7 +576,9 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR, NARROW>::NT), (Stage
     for (int k = 0; k < nchunks; ++k) {
         const int s = (kbase + k) % STAGES;
         const bool arrived = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((kbase + k) / STAGES) & 1));
-        const unsigned char* stage = smem + s * Cfg::STAGE_BYTES;
+        unsigned char* const stage = smem + s * Cfg::STAGE_BYTES;
+        // the stage of chunk k-1 (results of its last two cells land there)
+        unsigned char* const stage_prev = smem + ((s + STAGES - 1) % STAGES) * Cfg::STAGE_BYTES;
         const int jlo = k == 0 ? 2 : 0;                // cells a, a+1 came directly
         const int jhi = min(C, b - (a + k * C));       // cells from b on come directly
         // Cells come straight from shared memory as they are marched over;
@@ -616,7 +617,9 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR, NARROW>::NT), (Stage
                 put_global(a + k * C + j - 2, qn);
                 continue;
             }
-            put_stage(a + k * C + j - 2, qn);
+            // cell a + k*C + j - 2: position j - 2 of chunk k, or j + C - 2
+            // of chunk k - 1 (j < 2)
+            put_stage(j >= 2 ? stage : stage_prev, (j + C - 2) & (C - 1), qn);
             if (j == 1) {
                 // output chunk k-1 is complete in its stage: write it back; the
                 // write-back issued one chunk ago has had time to read its
@@ -667,10 +670,10 @@ __global__ void __launch_bounds__((StageCfg<Sys, Real, DIR, NARROW>::NT), (Stage
         V qn[NQ];
         load_direct(b, c1);
         step(c1, true, true, qn);
-        if (DIR == 0 && Cfg::XWB) put_stage(b - 2, qn); else put_global(b - 2, qn);
+        if (DIR == 0 && Cfg::XWB) put_stage(stage_of((b - 2 - a) / C), (b - 2 - a) % C, qn); else put_global(b - 2, qn);
         load_direct(b + 1, c1);
         step(c1, false, true, qn);
-        if (DIR == 0 && Cfg::XWB) put_stage(b - 1, qn); else put_global(b - 1, qn);
+        if (DIR == 0 && Cfg::XWB) put_stage(stage_of((b - 1 - a) / C), (b - 1 - a) % C, qn); else put_global(b - 1, qn);
     }
     if (DIR == 0 && Cfg::XWB) {
         // write back the output chunks still in their stages (a tail past b
