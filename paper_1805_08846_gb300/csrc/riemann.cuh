@@ -219,6 +219,26 @@ struct Acoustics {
 // where the rarely true last one holds (a supercritical middle state; in
 // subcritical flow the whole test is one packed quantity and a compare).
 // ------------------------------------------------------------------------
+// The subsonic shortcut's test from sign bits alone, for every lane: s1 < 0
+// (sign set), s3 > 0 (sign clear) and both middle-state tests hu^2 - g h^3
+// negative (sign set).  A zero of either sign only ever sends a lane to the
+// full solver, whose result is then the same; one AND of the bit patterns
+// replaces six compares.
+__device__ __forceinline__ bool subsonic_signs(float s1, float s3, float a, float b) {
+    return (int)(__float_as_uint(s1) & ~__float_as_uint(s3) & __float_as_uint(a) & __float_as_uint(b)) < 0;
+}
+__device__ __forceinline__ bool subsonic_signs(double s1, double s3, double a, double b) {
+    return (__double_as_longlong(s1) & ~__double_as_longlong(s3) & __double_as_longlong(a) &
+            __double_as_longlong(b)) < 0;
+}
+__device__ __forceinline__ bool subsonic_signs(f2 s1, f2 s3, f2 a, f2 b) {
+    const unsigned x = __float_as_uint(s1.v.x) & ~__float_as_uint(s3.v.x) & __float_as_uint(a.v.x) &
+                       __float_as_uint(b.v.x);
+    const unsigned y = __float_as_uint(s1.v.y) & ~__float_as_uint(s3.v.y) & __float_as_uint(a.v.y) &
+                       __float_as_uint(b.v.y);
+    return (int)(x & y) < 0;
+}
+
 template <class Real>   // double, float, or f2 (two lines)
 struct ShallowWater {
     using Value = Real;
@@ -320,7 +340,7 @@ struct ShallowWater {
             const Real hm3 = r.q[0] - w.W[2][0], hum3 = r.q[1] - w.W[2][1];
             const Real sup1 = vfma(hum1, hum1, (ng * hm1) * (hm1 * hm1));
             const Real sup3 = vfma(hum3, hum3, (ng * hm3) * (hm3 * hm3));
-            const bool lane_sub = !any(!vlt(vabs(uh), ch)) && !any(vgt(sup1, Real(0))) && !any(vgt(sup3, Real(0)));
+            const bool lane_sub = subsonic_signs(s1, s3, sup1, sup3);
             if (__all_sync(0xffffffffu, lane_sub)) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
