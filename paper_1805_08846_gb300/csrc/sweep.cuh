@@ -213,10 +213,13 @@ struct StageCfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 64;  // + alignment, barriers
     // register budget: 4 CTAs of 128 threads per SM for FP32 (measured best:
     // a 5-CTA budget forces worse schedules), 2 for FP64; 6 CTAs of 64
-    // two-line threads for the packed form (7 fit at run time)
+    // two-line threads for the packed y / z sweeps; 8 one-warp CTAs for the
+    // packed x sweep, which its best segment lengths fill anyway (188
+    // registers; measured against a 12-CTA budget at 166: 4096^2 x sweep
+    // 0.1134 -> 0.1124 ms, the 256-grid ensemble's x sweep 0.746 -> 0.657 ms)
     // (the same per-SM budget for narrow tiles: twice as many CTAs)
     static constexpr int MIN_CTAS =
-        (PK == 2 ? (DIR == 0 ? 12 : 6) : (sizeof(Real) == 4 ? 4 : 2)) * ((NARROW && !(PK == 2 && DIR == 0)) ? 2 : 1);
+        (PK == 2 ? (DIR == 0 ? 8 : 6) : (sizeof(Real) == 4 ? 4 : 2)) * ((NARROW && !(PK == 2 && DIR == 0)) ? 2 : 1);
 };
 
 template <class Sys, class Real, int LIM, int DIR, bool NARROW>
