@@ -24,10 +24,11 @@
 // deep enough without any per-thread prefetch registers.  For the y and z
 // sweeps a chunk is C rows of kLines consecutive x (one 512 B row per field
 // for FP32) and results are stored directly (a warp writes 32 consecutive x).
-// For the x sweep a chunk is 32 bytes of each of kLines rows (32-byte
-// swizzle, conflict-free 16-byte reads), and each row's results are gathered
-// into 16-byte words in registers and written as whole words.  The two cells
-// before and after the segment (ghosts at the domain edge) are read directly.
+// For the x sweep a chunk is 32 bytes of each of the tile's rows (32-byte
+// swizzle); each result overwrites an input position of its stage that has
+// been consumed, and a completed chunk leaves by a bulk-tensor store.  The two
+// cells before and after the segment (ghosts at the domain edge) are read
+// directly.
 #pragma once
 #include "claw_types.cuh"
 #include "riemann.cuh"
@@ -178,8 +179,10 @@ __global__ void __launch_bounds__(kLines) speed_kernel(const SweepArgs A, const 
 // A plane box holds 32 bytes' worth of cells (8 FP32 / 4 FP64) of 128
 // lines, 4 KB: for the y, z sweeps C rows of 128 adjacent x, for the x sweep
 // 32 bytes of each of 128 rows, kept with the 32-byte swizzle (the two
-// 16-byte halves of a row swap places on bit 2 of the row) so that a warp's
-// 16-byte reads of its own rows hit every bank once.
+// 16-byte halves of a row swap places on bit 2 of the row), under which a
+// warp's 16-byte reads of its own rows hit every bank once; the march reads
+// one cell (4 bytes) per row, which meets 4-way conflicts (rows r, r+8,
+// r+16, r+24 share banks; measured cheaper than reading 16-byte words).
 // Tile widths a direction's sweep offers (the autotuner picks one): NARROW
 // halves the lines per tile (fewer lanes past the edge of small or uneven
 // grids, more tiles); the two-line x sweep has only its 64-row tiles.
