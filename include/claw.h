@@ -123,7 +123,10 @@ typedef enum { CLAW_SPLIT_GODUNOV = 0, CLAW_SPLIT_STRANG = 1, CLAW_SPLIT_UNSPLIT
  * precision: 32 or 64; max_retries: consecutive rejections before
  * CLAW_ECFL (<= 0 selects 8); splitting: a claw_splitting; dry_tol
  * (CLAW_SHALLOW_WATER_DRY, >= 0): a cell with h <= dry_tol is dry (in FP32
- * at least every depth below the smallest normal float, 1.2e-38). */
+ * at least every depth below the smallest normal float, 1.2e-38).  Keep it
+ * well above rounding (e.g. 1e-3 of the depth scale): with dry_tol near 0 a
+ * draining film can round below zero, which stops the run with
+ * CLAW_ENONPHYS. */
 typedef struct {
     double rho, K, g;
     double cfl_desired, cfl_max, dt_max;
